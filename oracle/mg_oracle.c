@@ -1,0 +1,897 @@
+/*
+ * mg_oracle.c -- plain FP64 CPU oracle for the leading-order squared matrix
+ * element |M|^2, summed over helicities and colours, per event.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+ * legs of bench.py load this library.  It shares no code, header, table or
+ * constant generator with the CUDA path, and the CUDA path never calls it.
+ *
+ * What is computed (paper Sect. 1: the matrix element of a Monte Carlo event
+ * generator, computed per event from Feynman diagrams and helicity
+ * amplitudes; Sect. 3: its double-precision reference):
+ *
+ *   ME = (1/IDEN) * sum_{spin states} sum_{colours} |M|^2
+ *
+ * with IDEN = initial spin x colour average x final identical-particle
+ * factor.  The oracle evaluates the same quantity by an independent exact
+ * method:
+ *
+ *   - e+ e- -> mu+ mu-: the two s-channel diagrams (photon, Z) written out
+ *     with explicit 4x4 Dirac matrices;
+ *   - g g -> t t~ + (n-2) g: colour decomposition on one quark line,
+ *       M = sum_{sigma in S_n} (T^{a_sigma1} ... T^{a_sigman})_{i_t j_tbar} A(sigma),
+ *     partial amplitudes A(sigma) from colour-ordered Berends-Giele recursion
+ *     (the alternative to diagrams that the paper cites in Sect. 1), and the
+ *     colour sum  sum_col |M|^2 = sum_{sigma,tau} A(sigma)^* C(sigma,tau) A(tau)
+ *     with C built from explicit index sums over Gell-Mann matrices.
+ *
+ * Feynman rules (Peskin & Schroeder conventions, D = d - i g_s T^a A^a):
+ *   quark-gluon vertex  i g gamma^mu T^a
+ *   three-gluon vertex  g f^{abc} [g^{mu nu}(k-p)^rho + g^{nu rho}(p-q)^mu + g^{rho mu}(q-k)^nu]
+ *   four-gluon vertex   -i g^2 [f^{abe}f^{cde}(g^{mu rho}g^{nu sigma} - g^{mu sigma}g^{nu rho}) + ...]
+ *   gluon propagator    -i g_{mu nu} / P^2          (Feynman gauge)
+ *   top propagator      i (P-slash + m) / (P^2 - m^2 + i m Gamma)   (every top propagator)
+ * Substituting f^{abc} T^c = -i [T^a, T^b] gives the colour-ordered current
+ *   J(1..m) = (1/P^2) [ -g sum_k V3(J(1..k), J(k+1..m))
+ *                       + g^2 sum_{k<l} (2 (J_L.J_R) J_M - (J_L.J_M) J_R - (J_M.J_R) J_L) ]
+ *   V3(a,b) = (J_a.J_b)(k_a-k_b) + J_b (2k_b+k_a).J_a - J_a (2k_a+k_b).J_b
+ * (all gluon momenta incoming).  External states: Dirac-representation
+ * spinors in the spin-z basis (Bjorken-Drell normalisation, ubar u = 2m) and
+ * real linear gluon polarisations with eps^0 = 0, eps.k = 0 in the lab frame.
+ * Any complete basis gives the same spin sum.
+ *
+ * Pins (tests/): closed-form e+e- -> mu+mu- (photon and photon+Z), the
+ * analytic g g -> t t~ result, Ward identities of every partial amplitude,
+ * Bose symmetry, Lorentz invariance, spinor/polarisation completeness,
+ * Gell-Mann algebra identities and a colour-dressed recursion with explicit
+ * f^{abc} summed over every colour assignment.
+ */
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define MGO_OK 0
+#define MGO_ERR_ARG (-1)
+#define MGO_ERR_NOMEM (-2)
+
+enum { MGO_EEMUMU = 0, MGO_GGTT = 1, MGO_GGTTG = 2, MGO_GGTTGG = 3, MGO_GGTTGGG = 4 };
+
+#define MAXG 5     /* at most 5 gluons */
+#define MAXPERM 120
+
+typedef struct {
+  double mt, wt, alpha_s, mz, wz, alpha_em_inv, gf;
+  int photon_only;
+} oparams;
+
+static void unpack_params(const double* p, oparams* o) {
+  o->mt = p[0];
+  o->wt = p[1];
+  o->alpha_s = p[2];
+  o->mz = p[3];
+  o->wz = p[4];
+  o->alpha_em_inv = p[5];
+  o->gf = p[6];
+  o->photon_only = (p[7] != 0.0);
+}
+
+/* ------------------------------------------------------------------ */
+/* Lorentz and Dirac algebra, Dirac representation                    */
+/* ------------------------------------------------------------------ */
+
+static cplx GAM[4][4][4]; /* GAM[mu] = gamma^mu                   */
+static cplx GAM5[4][4];   /* gamma^5 = i g0 g1 g2 g3               */
+static cplx TGEN[8][3][3]; /* T^a = lambda^a / 2                   */
+
+static void matmul4(const cplx a[4][4], const cplx b[4][4], cplx c[4][4]) {
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) {
+      cplx s = 0;
+      for (int k = 0; k < 4; k++) s += a[i][k] * b[k][j];
+      c[i][j] = s;
+    }
+}
+
+__attribute__((constructor)) static void init_tables(void) {
+  memset(GAM, 0, sizeof(GAM));
+  /* gamma^0 = diag(1,1,-1,-1); gamma^i = [[0, sigma_i], [-sigma_i, 0]] */
+  GAM[0][0][0] = 1; GAM[0][1][1] = 1; GAM[0][2][2] = -1; GAM[0][3][3] = -1;
+  const cplx sig[3][2][2] = {{{0, 1}, {1, 0}}, {{0, -I}, {I, 0}}, {{1, 0}, {0, -1}}};
+  for (int i = 0; i < 3; i++)
+    for (int r = 0; r < 2; r++)
+      for (int c = 0; c < 2; c++) {
+        GAM[i + 1][r][c + 2] = sig[i][r][c];
+        GAM[i + 1][r + 2][c] = -sig[i][r][c];
+      }
+  cplx t1[4][4], t2[4][4];
+  matmul4((const cplx(*)[4])GAM[0], (const cplx(*)[4])GAM[1], t1);
+  matmul4((const cplx(*)[4])t1, (const cplx(*)[4])GAM[2], t2);
+  matmul4((const cplx(*)[4])t2, (const cplx(*)[4])GAM[3], t1);
+  for (int r = 0; r < 4; r++)
+    for (int c = 0; c < 4; c++) GAM5[r][c] = I * t1[r][c];
+
+  /* Gell-Mann matrices, T^a = lambda^a / 2 */
+  memset(TGEN, 0, sizeof(TGEN));
+  TGEN[0][0][1] = 0.5; TGEN[0][1][0] = 0.5;
+  TGEN[1][0][1] = -0.5 * I; TGEN[1][1][0] = 0.5 * I;
+  TGEN[2][0][0] = 0.5; TGEN[2][1][1] = -0.5;
+  TGEN[3][0][2] = 0.5; TGEN[3][2][0] = 0.5;
+  TGEN[4][0][2] = -0.5 * I; TGEN[4][2][0] = 0.5 * I;
+  TGEN[5][1][2] = 0.5; TGEN[5][2][1] = 0.5;
+  TGEN[6][1][2] = -0.5 * I; TGEN[6][2][1] = 0.5 * I;
+  const double r3 = 1.0 / (2.0 * sqrt(3.0));
+  TGEN[7][0][0] = r3; TGEN[7][1][1] = r3; TGEN[7][2][2] = -2.0 * r3;
+}
+
+static const double METRIC[4] = {1.0, -1.0, -1.0, -1.0};
+
+static cplx dot_cc(const cplx a[4], const cplx b[4]) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+static cplx dot_rc(const double a[4], const cplx b[4]) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+static double dot_rr(const double a[4], const double b[4]) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+/* S = gamma^mu v_mu for a contravariant complex vector v */
+static void slash_c(const cplx v[4], cplx S[4][4]) {
+  for (int r = 0; r < 4; r++)
+    for (int c = 0; c < 4; c++) {
+      cplx s = 0;
+      for (int mu = 0; mu < 4; mu++) s += METRIC[mu] * GAM[mu][r][c] * v[mu];
+      S[r][c] = s;
+    }
+}
+static void slash_r(const double v[4], cplx S[4][4]) {
+  cplx vc[4] = {v[0], v[1], v[2], v[3]};
+  slash_c(vc, S);
+}
+
+/* row vector times matrix */
+static void rowmat(const cplx r[4], const cplx M[4][4], cplx out[4]) {
+  for (int c = 0; c < 4; c++) {
+    cplx s = 0;
+    for (int k = 0; k < 4; k++) s += r[k] * M[k][c];
+    out[c] = s;
+  }
+}
+static void matcol(const cplx M[4][4], const cplx v[4], cplx out[4]) {
+  for (int r = 0; r < 4; r++) {
+    cplx s = 0;
+    for (int k = 0; k < 4; k++) s += M[r][k] * v[k];
+    out[r] = s;
+  }
+}
+static cplx rowcol(const cplx r[4], const cplx c[4]) {
+  cplx s = 0;
+  for (int k = 0; k < 4; k++) s += r[k] * c[k];
+  return s;
+}
+
+/* ------------------------------------------------------------------ */
+/* External states                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Dirac spinor u(p, s), spin-z basis chi_1 = (1,0), chi_2 = (0,1):
+ *   u = [ sqrt(E+m) chi ; (sigma.p) chi / sqrt(E+m) ]                 */
+static void spinor_u(const double p[4], double m, int s, cplx u[4]) {
+  const double a = sqrt(p[0] + m);
+  const cplx chi[2] = {s == 0 ? 1.0 : 0.0, s == 0 ? 0.0 : 1.0};
+  /* sigma.p = [[pz, px - i py], [px + i py, -pz]] */
+  const cplx sp0 = p[3] * chi[0] + (p[1] - I * p[2]) * chi[1];
+  const cplx sp1 = (p[1] + I * p[2]) * chi[0] - p[3] * chi[1];
+  u[0] = a * chi[0];
+  u[1] = a * chi[1];
+  u[2] = sp0 / a;
+  u[3] = sp1 / a;
+}
+/* v(p, s) = [ (sigma.p) eta / sqrt(E+m) ; sqrt(E+m) eta ] */
+static void spinor_v(const double p[4], double m, int s, cplx v[4]) {
+  const double a = sqrt(p[0] + m);
+  const cplx eta[2] = {s == 0 ? 1.0 : 0.0, s == 0 ? 0.0 : 1.0};
+  const cplx sp0 = p[3] * eta[0] + (p[1] - I * p[2]) * eta[1];
+  const cplx sp1 = (p[1] + I * p[2]) * eta[0] - p[3] * eta[1];
+  v[0] = sp0 / a;
+  v[1] = sp1 / a;
+  v[2] = a * eta[0];
+  v[3] = a * eta[1];
+}
+/* Dirac adjoint psibar = psi^dagger gamma^0 */
+static void dirac_bar(const cplx in[4], cplx out[4]) {
+  out[0] = conj(in[0]);
+  out[1] = conj(in[1]);
+  out[2] = -conj(in[2]);
+  out[3] = -conj(in[3]);
+}
+
+/* Real linear polarisation vectors of a massless vector with momentum k:
+ * eps^0 = 0, eps.k = 0, orthonormal.  e1 = unit(n x khat) with n the
+ * coordinate axis least aligned with k, e2 = khat x e1.                 */
+static void polarisation(const double k[4], int which, double eps[4]) {
+  const double kk = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+  const double kh[3] = {k[1] / kk, k[2] / kk, k[3] / kk};
+  int ax = 0;
+  for (int i = 1; i < 3; i++)
+    if (fabs(kh[i]) < fabs(kh[ax])) ax = i;
+  double n[3] = {0, 0, 0};
+  n[ax] = 1.0;
+  double e1[3] = {n[1] * kh[2] - n[2] * kh[1], n[2] * kh[0] - n[0] * kh[2], n[0] * kh[1] - n[1] * kh[0]};
+  const double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (int i = 0; i < 3; i++) e1[i] /= l1;
+  const double e2[3] = {kh[1] * e1[2] - kh[2] * e1[1], kh[2] * e1[0] - kh[0] * e1[2], kh[0] * e1[1] - kh[1] * e1[0]};
+  eps[0] = 0.0;
+  for (int i = 0; i < 3; i++) eps[i + 1] = (which == 0) ? e1[i] : e2[i];
+}
+
+/* ------------------------------------------------------------------ */
+/* Permutations (lexicographic order)                                  */
+/* ------------------------------------------------------------------ */
+
+static int factorial(int n) {
+  int f = 1;
+  for (int i = 2; i <= n; i++) f *= i;
+  return f;
+}
+
+static int next_permutation(int* a, int n) {
+  int i = n - 2;
+  while (i >= 0 && a[i] >= a[i + 1]) i--;
+  if (i < 0) return 0;
+  int j = n - 1;
+  while (a[j] <= a[i]) j--;
+  int t = a[i]; a[i] = a[j]; a[j] = t;
+  for (int l = i + 1, r = n - 1; l < r; l++, r--) { t = a[l]; a[l] = a[r]; a[r] = t; }
+  return 1;
+}
+
+int mgo_permutations(int n, int* perms) {
+  if (n < 1 || n > MAXG) return MGO_ERR_ARG;
+  int a[MAXG];
+  for (int i = 0; i < n; i++) a[i] = i;
+  int k = 0;
+  do {
+    for (int i = 0; i < n; i++) perms[k * n + i] = a[i];
+    k++;
+  } while (next_permutation(a, n));
+  return MGO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Colour matrix by explicit Gell-Mann index sums                      */
+/*   C(sigma,tau) = sum_{a_1..a_n} sum_{i,j}                           */
+/*        (T^{a_sigma1}..T^{a_sigman})_{ij} conj((T^{a_tau1}..T^{a_taun})_{ij}) */
+/* ------------------------------------------------------------------ */
+
+static void matmul3(const cplx a[3][3], const cplx b[3][3], cplx c[3][3]) {
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) c[i][j] = a[i][0] * b[0][j] + a[i][1] * b[1][j] + a[i][2] * b[2][j];
+}
+
+static int colour_matrix_compute(int n, cplx* C) {
+  const int np = factorial(n);
+  int* perms = (int*)malloc(sizeof(int) * np * n);
+  cplx(*W)[3][3] = malloc(sizeof(cplx) * 9 * np);
+  if (!perms || !W) { free(perms); free(W); return MGO_ERR_NOMEM; }
+  mgo_permutations(n, perms);
+  memset(C, 0, sizeof(cplx) * np * np);
+  int a[MAXG];
+  long total = 1;
+  for (int i = 0; i < n; i++) total *= 8;
+  for (long code = 0; code < total; code++) {
+    long c = code;
+    for (int i = 0; i < n; i++) { a[i] = (int)(c % 8); c /= 8; }
+    for (int s = 0; s < np; s++) {
+      const int* p = perms + s * n;
+      cplx acc[3][3], tmp[3][3];
+      memcpy(acc, TGEN[a[p[0]]], sizeof(acc));
+      for (int l = 1; l < n; l++) {
+        matmul3((const cplx(*)[3])acc, (const cplx(*)[3])TGEN[a[p[l]]], tmp);
+        memcpy(acc, tmp, sizeof(acc));
+      }
+      memcpy(W[s], acc, sizeof(acc));
+    }
+    for (int s = 0; s < np; s++)
+      for (int t = s; t < np; t++) {
+        cplx sum = 0;
+        for (int i = 0; i < 3; i++)
+          for (int j = 0; j < 3; j++) sum += W[s][i][j] * conj(W[t][i][j]);
+        C[s * np + t] += sum;
+      }
+  }
+  for (int s = 0; s < np; s++)
+    for (int t = 0; t < s; t++) C[s * np + t] = conj(C[t * np + s]);
+  free(perms);
+  free(W);
+  return MGO_OK;
+}
+
+/* cached per n; computed once under a lock */
+static cplx* colour_cache[MAXG + 1];
+static pthread_mutex_t colour_lock = PTHREAD_MUTEX_INITIALIZER;
+
+static const cplx* colour_matrix(int n) {
+  pthread_mutex_lock(&colour_lock);
+  if (!colour_cache[n]) {
+    const int np = factorial(n);
+    cplx* C = (cplx*)malloc(sizeof(cplx) * np * np);
+    if (C && colour_matrix_compute(n, C) == MGO_OK) colour_cache[n] = C;
+    else free(C);
+  }
+  const cplx* r = colour_cache[n];
+  pthread_mutex_unlock(&colour_lock);
+  return r;
+}
+
+int mgo_colour_matrix(int n, double* out /* complex [n!][n!] interleaved */) {
+  if (n < 1 || n > MAXG) return MGO_ERR_ARG;
+  const cplx* C = colour_matrix(n);
+  if (!C) return MGO_ERR_NOMEM;
+  const int np = factorial(n);
+  memcpy(out, C, sizeof(cplx) * np * np);
+  return MGO_OK;
+}
+
+int mgo_generators(double* out /* complex [8][3][3] */) {
+  memcpy(out, TGEN, sizeof(TGEN));
+  return MGO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Colour-ordered Berends-Giele recursion                              */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int n;                      /* number of gluons                         */
+  double k[MAXG][4];          /* incoming gluon momenta, by gluon index  */
+  cplx eps[MAXG][4];          /* gluon wavefunctions, by gluon index     */
+  double pt[4], ptb[4];       /* outgoing top / antitop momenta          */
+  cplx ubar[4];               /* Dirac adjoint spinor of the top         */
+  cplx v[4];                  /* spinor of the antitop                   */
+  double g, mt, wt;
+} qline;
+
+/* V3(a,b) = (Ja.Jb)(ka-kb) + Jb (2kb+ka).Ja - Ja (2ka+kb).Jb */
+static void vertex3(const double ka[4], const cplx ja[4], const double kb[4], const cplx jb[4], cplx out[4]) {
+  double x[4], y[4];
+  for (int mu = 0; mu < 4; mu++) {
+    x[mu] = 2.0 * kb[mu] + ka[mu];
+    y[mu] = 2.0 * ka[mu] + kb[mu];
+  }
+  const cplx jab = dot_cc(ja, jb);
+  const cplx xa = dot_rc(x, ja);
+  const cplx yb = dot_rc(y, jb);
+  for (int mu = 0; mu < 4; mu++) out[mu] = jab * (ka[mu] - kb[mu]) + jb[mu] * xa - ja[mu] * yb;
+}
+
+/* ordered quartic piece: 2(L.R) M - (L.M) R - (M.R) L */
+static void vertex4(const cplx l[4], const cplx m[4], const cplx r[4], cplx out[4]) {
+  const cplx lr = dot_cc(l, r), lm = dot_cc(l, m), mr = dot_cc(m, r);
+  for (int mu = 0; mu < 4; mu++) out[mu] = 2.0 * lr * m[mu] - lm * r[mu] - mr * l[mu];
+}
+
+/* Partial amplitude A(sigma) for one ordering sigma of the gluons. */
+static cplx ordered_amplitude(const qline* q, const int* sigma) {
+  const int n = q->n;
+  cplx J[MAXG][MAXG][4];
+  double K[MAXG][MAXG][4];
+  for (int i = 0; i < n; i++) {
+    for (int mu = 0; mu < 4; mu++) {
+      J[i][i][mu] = q->eps[sigma[i]][mu];
+      K[i][i][mu] = q->k[sigma[i]][mu];
+    }
+  }
+  for (int len = 2; len <= n; len++) {
+    for (int i = 0; i + len - 1 < n; i++) {
+      const int j = i + len - 1;
+      for (int mu = 0; mu < 4; mu++) K[i][j][mu] = K[i][j - 1][mu] + K[j][j][mu];
+      cplx acc[4] = {0, 0, 0, 0}, t[4];
+      for (int m = i; m < j; m++) {
+        vertex3(K[i][m], J[i][m], K[m + 1][j], J[m + 1][j], t);
+        for (int mu = 0; mu < 4; mu++) acc[mu] += -q->g * t[mu];
+      }
+      for (int m1 = i; m1 < j; m1++)
+        for (int m2 = m1 + 1; m2 < j; m2++) {
+          vertex4(J[i][m1], J[m1 + 1][m2], J[m2 + 1][j], t);
+          for (int mu = 0; mu < 4; mu++) acc[mu] += q->g * q->g * t[mu];
+        }
+      const double p2 = dot_rr(K[i][j], K[i][j]);
+      for (int mu = 0; mu < 4; mu++) J[i][j][mu] = acc[mu] / p2;
+    }
+  }
+  /* quark line: Psi[k] = row current with the first k gluons of sigma attached */
+  cplx Psi[MAXG][4];
+  for (int c = 0; c < 4; c++) Psi[0][c] = q->ubar[c];
+  for (int k = 1; k < n; k++) {
+    double Q[4];
+    for (int mu = 0; mu < 4; mu++) Q[mu] = q->pt[mu] - K[0][k - 1][mu];
+    const cplx den = dot_rr(Q, Q) - q->mt * q->mt + I * q->mt * q->wt;
+    cplx row[4] = {0, 0, 0, 0}, t[4];
+    for (int m = 0; m < k; m++) {
+      cplx S[4][4];
+      slash_c(J[m][k - 1], S);
+      rowmat(Psi[m], (const cplx(*)[4])S, t);
+      for (int c = 0; c < 4; c++) row[c] += t[c];
+    }
+    cplx P[4][4];
+    slash_r(Q, P);
+    for (int c = 0; c < 4; c++) P[c][c] += q->mt;
+    rowmat(row, (const cplx(*)[4])P, t);
+    /* (i g) from the vertex, i / den from the propagator */
+    for (int c = 0; c < 4; c++) Psi[k][c] = (I * q->g) * (I / den) * t[c];
+  }
+  cplx amp = 0;
+  for (int m = 0; m < n; m++) {
+    cplx S[4][4], t[4];
+    slash_c(J[m][n - 1], S);
+    matcol((const cplx(*)[4])S, q->v, t);
+    amp += (I * q->g) * rowcol(Psi[m], t);
+  }
+  return amp;
+}
+
+static void all_ordered_amplitudes(const qline* q, cplx* amps) {
+  const int n = q->n;
+  int a[MAXG];
+  for (int i = 0; i < n; i++) a[i] = i;
+  int s = 0;
+  do {
+    amps[s++] = ordered_amplitude(q, a);
+  } while (next_permutation(a, n));
+}
+
+static int fill_qline(qline* q, int n, const double* params, const double* kin, const double* eps, const double* pt,
+                      const double* ubar, const double* ptb, const double* v) {
+  if (n < 1 || n > MAXG) return MGO_ERR_ARG;
+  oparams o;
+  unpack_params(params, &o);
+  q->n = n;
+  q->g = sqrt(4.0 * M_PI * o.alpha_s);
+  q->mt = o.mt;
+  q->wt = o.wt;
+  for (int i = 0; i < n; i++)
+    for (int mu = 0; mu < 4; mu++) {
+      q->k[i][mu] = kin[4 * i + mu];
+      q->eps[i][mu] = eps[8 * i + 2 * mu] + I * eps[8 * i + 2 * mu + 1];
+    }
+  for (int mu = 0; mu < 4; mu++) {
+    q->pt[mu] = pt[mu];
+    q->ptb[mu] = ptb[mu];
+    q->ubar[mu] = ubar[2 * mu] + I * ubar[2 * mu + 1];
+    q->v[mu] = v[2 * mu] + I * v[2 * mu + 1];
+  }
+  return MGO_OK;
+}
+
+/* Partial amplitudes for explicit external wavefunctions (test hook):
+ * kin = incoming gluon momenta [n][4]; eps complex [n][4]; ubar, v complex [4]. */
+int mgo_ordered_amps(int n, const double* params, const double* kin, const double* eps, const double* pt,
+                     const double* ubar, const double* ptb, const double* v, double* amps_out) {
+  qline q;
+  int rc = fill_qline(&q, n, params, kin, eps, pt, ubar, ptb, v);
+  if (rc) return rc;
+  all_ordered_amplitudes(&q, (cplx*)amps_out);
+  return MGO_OK;
+}
+
+/* sum_{sigma,tau} A^*(sigma) C(sigma,tau) A(tau) for explicit external states */
+int mgo_ordered_colour_sum(int n, const double* params, const double* kin, const double* eps, const double* pt,
+                           const double* ubar, const double* ptb, const double* v, double* out) {
+  qline q;
+  int rc = fill_qline(&q, n, params, kin, eps, pt, ubar, ptb, v);
+  if (rc) return rc;
+  const cplx* C = colour_matrix(n);
+  if (!C) return MGO_ERR_NOMEM;
+  const int np = factorial(n);
+  cplx A[MAXPERM];
+  all_ordered_amplitudes(&q, A);
+  cplx s = 0;
+  for (int i = 0; i < np; i++)
+    for (int j = 0; j < np; j++) s += conj(A[i]) * C[i * np + j] * A[j];
+  *out = creal(s);
+  return MGO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Colour-dressed recursion (pin for the colour decomposition)         */
+/* Full Feynman rules with explicit f^{abc} and T^a, currents over     */
+/* gluon subsets, summed over every colour assignment of the externals.*/
+/* ------------------------------------------------------------------ */
+
+static double FABC[8][8][8];
+static int fabc_ready = 0;
+static pthread_mutex_t fabc_lock = PTHREAD_MUTEX_INITIALIZER;
+
+/* f^{abc} = -2 i Tr([T^a, T^b] T^c) */
+static void init_fabc(void) {
+  pthread_mutex_lock(&fabc_lock);
+  if (!fabc_ready) {
+    for (int a = 0; a < 8; a++)
+      for (int b = 0; b < 8; b++)
+        for (int c = 0; c < 8; c++) {
+          cplx ab[3][3], ba[3][3], x[3][3], y[3][3];
+          matmul3((const cplx(*)[3])TGEN[a], (const cplx(*)[3])TGEN[b], ab);
+          matmul3((const cplx(*)[3])TGEN[b], (const cplx(*)[3])TGEN[a], ba);
+          for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) x[i][j] = ab[i][j] - ba[i][j];
+          matmul3((const cplx(*)[3])x, (const cplx(*)[3])TGEN[c], y);
+          const cplx tr = y[0][0] + y[1][1] + y[2][2];
+          FABC[a][b][c] = creal(-2.0 * I * tr);
+        }
+    fabc_ready = 1;
+  }
+  pthread_mutex_unlock(&fabc_lock);
+}
+
+int mgo_fabc(double* out /* [8][8][8] */) {
+  init_fabc();
+  memcpy(out, FABC, sizeof(FABC));
+  return MGO_OK;
+}
+
+typedef struct {
+  cplx J[1 << MAXG][8][4]; /* J[subset][colour][mu] */
+  double K[1 << MAXG][4];
+  int have[1 << MAXG];
+} dressed_ws;
+
+static void dressed_current(const qline* q, const int* col, int S, dressed_ws* w) {
+  if (w->have[S]) return;
+  const int n = q->n;
+  for (int mu = 0; mu < 4; mu++) w->K[S][mu] = 0.0;
+  for (int i = 0; i < n; i++)
+    if (S & (1 << i))
+      for (int mu = 0; mu < 4; mu++) w->K[S][mu] += q->k[i][mu];
+  memset(w->J[S], 0, sizeof(w->J[S]));
+  if (__builtin_popcount(S) == 1) {
+    int i = __builtin_ctz(S);
+    for (int mu = 0; mu < 4; mu++) w->J[S][col[i]][mu] = q->eps[i][mu];
+    w->have[S] = 1;
+    return;
+  }
+  const double g = q->g;
+  cplx acc[8][4];
+  memset(acc, 0, sizeof(acc));
+  /* three-gluon vertex: unordered splits {S1, S2}; S1 holds the lowest member of S */
+  const int low = S & (-S);
+  for (int S1 = (S - 1) & S; S1 > 0; S1 = (S1 - 1) & S) {
+    if (!(S1 & low)) continue;
+    const int S2 = S ^ S1;
+    dressed_current(q, col, S1, w);
+    dressed_current(q, col, S2, w);
+    for (int a = 0; a < 8; a++)
+      for (int b = 0; b < 8; b++) {
+        cplx t[4];
+        vertex3(w->K[S1], w->J[S1][a], w->K[S2], w->J[S2][b], t);
+        for (int c = 0; c < 8; c++) {
+          const double f = FABC[a][b][c];
+          if (f == 0.0) continue;
+          /* (-i/P^2) * g f^{abc} V3 */
+          for (int mu = 0; mu < 4; mu++) acc[c][mu] += -I * g * f * t[mu];
+        }
+      }
+  }
+  /* four-gluon vertex: unordered splits {S1, S2, S3}, legs (a,mu) (b,nu) (d,rho), out (c,sigma):
+   *  -i g^2 [ f^{abe} f^{dce} (g^{mu rho} g^{nu sigma} - g^{mu sigma} g^{nu rho})
+   *         + f^{ade} f^{bce} (g^{mu nu} g^{rho sigma} - g^{mu sigma} g^{nu rho})
+   *         + f^{ace} f^{bde} (g^{mu nu} g^{rho sigma} - g^{mu rho} g^{nu sigma}) ] */
+  for (int S1 = (S - 1) & S; S1 > 0; S1 = (S1 - 1) & S) {
+    if (!(S1 & low)) continue;
+    const int R = S ^ S1;
+    const int low2 = R & (-R);
+    for (int S2 = (R - 1) & R; S2 > 0; S2 = (S2 - 1) & R) {
+      if (!(S2 & low2)) continue;
+      const int S3 = R ^ S2;
+      dressed_current(q, col, S1, w);
+      dressed_current(q, col, S2, w);
+      dressed_current(q, col, S3, w);
+      for (int a = 0; a < 8; a++)
+        for (int b = 0; b < 8; b++)
+          for (int d = 0; d < 8; d++) {
+            const cplx* j1 = w->J[S1][a];
+            const cplx* j2 = w->J[S2][b];
+            const cplx* j3 = w->J[S3][d];
+            const cplx d12 = dot_cc(j1, j2), d13 = dot_cc(j1, j3), d23 = dot_cc(j2, j3);
+            if (d12 == 0 && d13 == 0 && d23 == 0) continue;
+            for (int c = 0; c < 8; c++) {
+              double f1 = 0, f2 = 0, f3 = 0;
+              for (int e = 0; e < 8; e++) {
+                f1 += FABC[a][b][e] * FABC[d][c][e];
+                f2 += FABC[a][d][e] * FABC[b][c][e];
+                f3 += FABC[a][c][e] * FABC[b][d][e];
+              }
+              if (f1 == 0 && f2 == 0 && f3 == 0) continue;
+              for (int mu = 0; mu < 4; mu++) {
+                const cplx lor = f1 * (d13 * j2[mu] - d23 * j1[mu]) + f2 * (d12 * j3[mu] - d23 * j1[mu]) +
+                                 f3 * (d12 * j3[mu] - d13 * j2[mu]);
+                /* (-i/P^2) * (-i g^2) = -g^2 / P^2 */
+                acc[c][mu] += -g * g * lor;
+              }
+            }
+          }
+    }
+  }
+  const double p2 = dot_rr(w->K[S], w->K[S]);
+  for (int c = 0; c < 8; c++)
+    for (int mu = 0; mu < 4; mu++) w->J[S][c][mu] = acc[c][mu] / p2;
+  w->have[S] = 1;
+}
+
+/* sum over all external colours of |M|^2 for explicit external spin states */
+int mgo_dressed_colour_sum(int n, const double* params, const double* kin, const double* eps, const double* pt,
+                           const double* ubar, const double* ptb, const double* v, double* out) {
+  qline q;
+  int rc = fill_qline(&q, n, params, kin, eps, pt, ubar, ptb, v);
+  if (rc) return rc;
+  if (n > 4) return MGO_ERR_ARG;
+  init_fabc();
+  dressed_ws* w = (dressed_ws*)malloc(sizeof(dressed_ws));
+  if (!w) return MGO_ERR_NOMEM;
+  const int full = (1 << n) - 1;
+  int col[MAXG];
+  long total = 1;
+  for (int i = 0; i < n; i++) total *= 8;
+  double sum = 0.0;
+  for (long code = 0; code < total; code++) {
+    long c = code;
+    for (int i = 0; i < n; i++) { col[i] = (int)(c % 8); c /= 8; }
+    memset(w->have, 0, sizeof(w->have));
+    /* quark row currents Psi[S][colour i_open][4] over gluon subsets S, built
+     * from the top end: Psi[S] = sum_{B subset S} Psi[S\B] (i g Jslash^a(B) T^a) i(Qslash+m)/D */
+    static __thread cplx Psi[1 << MAXG][3][3][4]; /* [S][i_top][open colour][spinor] */
+    for (int it = 0; it < 3; it++)
+      for (int jo = 0; jo < 3; jo++)
+        for (int s4 = 0; s4 < 4; s4++) Psi[0][it][jo][s4] = (it == jo) ? q.ubar[s4] : 0.0;
+    for (int S = 1; S < full; S++) {
+      double Q[4];
+      for (int mu = 0; mu < 4; mu++) Q[mu] = q.pt[mu];
+      for (int i = 0; i < n; i++)
+        if (S & (1 << i))
+          for (int mu = 0; mu < 4; mu++) Q[mu] -= q.k[i][mu];
+      const cplx den = dot_rr(Q, Q) - q.mt * q.mt + I * q.mt * q.wt;
+      cplx P[4][4];
+      slash_r(Q, P);
+      for (int r = 0; r < 4; r++) P[r][r] += q.mt;
+      cplx row[3][3][4];
+      memset(row, 0, sizeof(row));
+      for (int B = S; B > 0; B = (B - 1) & S) {
+        const int A = S ^ B;
+        dressed_current(&q, col, B, w);
+        for (int a = 0; a < 8; a++) {
+          cplx Sl[4][4];
+          slash_c(w->J[B][a], Sl);
+          for (int it = 0; it < 3; it++)
+            for (int j = 0; j < 3; j++) {
+              cplx t[4];
+              rowmat(Psi[A][it][j], (const cplx(*)[4])Sl, t);
+              for (int k = 0; k < 3; k++) {
+                const cplx tc = TGEN[a][j][k];
+                if (tc == 0) continue;
+                for (int s4 = 0; s4 < 4; s4++) row[it][k][s4] += tc * t[s4];
+              }
+            }
+        }
+      }
+      for (int it = 0; it < 3; it++)
+        for (int k = 0; k < 3; k++) {
+          cplx t[4];
+          rowmat(row[it][k], (const cplx(*)[4])P, t);
+          for (int s4 = 0; s4 < 4; s4++) Psi[S][it][k][s4] = (I * q.g) * (I / den) * t[s4];
+        }
+    }
+    /* amplitude with open colours (i_top, j_antitop) */
+    cplx M[3][3];
+    memset(M, 0, sizeof(M));
+    for (int B = full; B > 0; B = (B - 1) & full) {
+      const int A = full ^ B;
+      dressed_current(&q, col, B, w);
+      for (int a = 0; a < 8; a++) {
+        cplx Sl[4][4], t[4];
+        slash_c(w->J[B][a], Sl);
+        matcol((const cplx(*)[4])Sl, q.v, t);
+        for (int it = 0; it < 3; it++)
+          for (int j = 0; j < 3; j++) {
+            const cplx r = rowcol(Psi[A][it][j], t);
+            for (int k = 0; k < 3; k++) M[it][k] += (I * q.g) * TGEN[a][j][k] * r;
+          }
+      }
+    }
+    for (int it = 0; it < 3; it++)
+      for (int k = 0; k < 3; k++) sum += creal(M[it][k] * conj(M[it][k]));
+  }
+  free(w);
+  *out = sum;
+  return MGO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* External-state test hooks                                           */
+/* ------------------------------------------------------------------ */
+
+int mgo_spinor(int kind /*0 u, 1 v, 2 ubar, 3 vbar*/, const double* p, double m, int s, double* out) {
+  cplx w[4], b[4];
+  if (kind == 0 || kind == 2) spinor_u(p, m, s, w);
+  else spinor_v(p, m, s, w);
+  if (kind >= 2) {
+    dirac_bar(w, b);
+    memcpy(out, b, sizeof(b));
+  } else {
+    memcpy(out, w, sizeof(w));
+  }
+  return MGO_OK;
+}
+
+int mgo_polarisation(const double* k, int which, double* out) {
+  polarisation(k, which, out);
+  return MGO_OK;
+}
+
+int mgo_gamma(double* out /* complex [5][4][4]: gamma^0..3, gamma^5 */) {
+  memcpy(out, GAM, sizeof(GAM));
+  memcpy(out + 2 * 64, GAM5, sizeof(GAM5));
+  return MGO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Full matrix elements                                                */
+/* ------------------------------------------------------------------ */
+
+/* e+(p1) e-(p2) -> mu+(p3) mu-(p4) through s-channel photon and Z */
+static double me_eemumu(const oparams* o, const double* mom) {
+  const double* p1 = mom;
+  const double* p2 = mom + 4;
+  const double* p3 = mom + 8;
+  const double* p4 = mom + 12;
+  const double alpha = 1.0 / o->alpha_em_inv;
+  const double ee = sqrt(4.0 * M_PI * alpha);
+  const double mz2 = o->mz * o->mz;
+  const double mw2 = 0.5 * mz2 + sqrt(0.25 * mz2 * mz2 - M_PI * alpha * mz2 / (M_SQRT2 * o->gf));
+  const double sw2 = 1.0 - mw2 / mz2;
+  const double cw2 = 1.0 - sw2;
+  const double gl = -0.5 + sw2, gr = sw2;                /* T3 - Q sw^2 for Q = -1 */
+  const double gz = ee / sqrt(sw2 * cw2);
+  double ptot[4];
+  for (int mu = 0; mu < 4; mu++) ptot[mu] = p1[mu] + p2[mu];
+  const double s = dot_rr(ptot, ptot);
+  const cplx prop_a = -I / s;
+  const cplx prop_z = o->photon_only ? 0.0 : -I / (s - mz2 + I * o->mz * o->wz);
+  /* Gamma_gamma^mu = -i e Q gamma^mu (Q = -1); Gamma_Z^mu = -i gz gamma^mu (gl PL + gr PR) */
+  cplx PL[4][4], PR[4][4];
+  for (int r = 0; r < 4; r++)
+    for (int c = 0; c < 4; c++) {
+      PL[r][c] = 0.5 * ((r == c ? 1.0 : 0.0) - GAM5[r][c]);
+      PR[r][c] = 0.5 * ((r == c ? 1.0 : 0.0) + GAM5[r][c]);
+    }
+  cplx GA[4][4][4], GZ[4][4][4];
+  for (int mu = 0; mu < 4; mu++) {
+    cplx chir[4][4], tmp[4][4];
+    for (int r = 0; r < 4; r++)
+      for (int c = 0; c < 4; c++) chir[r][c] = gl * PL[r][c] + gr * PR[r][c];
+    matmul4((const cplx(*)[4])GAM[mu], (const cplx(*)[4])chir, tmp);
+    for (int r = 0; r < 4; r++)
+      for (int c = 0; c < 4; c++) {
+        GA[mu][r][c] = -I * ee * (-1.0) * GAM[mu][r][c];
+        GZ[mu][r][c] = -I * gz * tmp[r][c];
+      }
+  }
+  double sum = 0.0;
+  for (int s1 = 0; s1 < 2; s1++)
+    for (int s2 = 0; s2 < 2; s2++)
+      for (int s3 = 0; s3 < 2; s3++)
+        for (int s4 = 0; s4 < 2; s4++) {
+          cplx v1[4], vb1[4], u2[4], v3[4], u4[4], ub4[4];
+          spinor_v(p1, 0.0, s1, v1);
+          dirac_bar(v1, vb1);
+          spinor_u(p2, 0.0, s2, u2);
+          spinor_v(p3, 0.0, s3, v3);
+          spinor_u(p4, 0.0, s4, u4);
+          dirac_bar(u4, ub4);
+          cplx ja[4], jz[4], la[4], lz[4];
+          for (int mu = 0; mu < 4; mu++) {
+            cplx t[4];
+            matcol((const cplx(*)[4])GA[mu], u2, t);
+            ja[mu] = rowcol(vb1, t);
+            matcol((const cplx(*)[4])GZ[mu], u2, t);
+            jz[mu] = rowcol(vb1, t);
+            matcol((const cplx(*)[4])GA[mu], v3, t);
+            la[mu] = rowcol(ub4, t);
+            matcol((const cplx(*)[4])GZ[mu], v3, t);
+            lz[mu] = rowcol(ub4, t);
+          }
+          const cplx m = dot_cc(ja, la) * prop_a + dot_cc(jz, lz) * prop_z;
+          sum += creal(m * conj(m));
+        }
+  return sum / 4.0;
+}
+
+/* g(p1) g(p2) -> t(p3) t~(p4) g(p5) ... : n gluons in total */
+static double me_ggtt_ng(const oparams* o, int n, const double* mom) {
+  const cplx* C = colour_matrix(n);
+  if (!C) return NAN;
+  const int np = factorial(n);
+  /* gluon index -> particle slot; initial gluons 0,1 then final gluons 4.. */
+  int slot[MAXG];
+  slot[0] = 0;
+  slot[1] = 1;
+  for (int i = 2; i < n; i++) slot[i] = i + 2;
+  qline q;
+  q.n = n;
+  q.g = sqrt(4.0 * M_PI * o->alpha_s);
+  q.mt = o->mt;
+  q.wt = o->wt;
+  for (int mu = 0; mu < 4; mu++) {
+    q.pt[mu] = mom[8 + mu];
+    q.ptb[mu] = mom[12 + mu];
+  }
+  double pol[MAXG][2][4];
+  for (int i = 0; i < n; i++) {
+    const double* p = mom + 4 * slot[i];
+    const double sign = (slot[i] < 2) ? 1.0 : -1.0; /* incoming momentum */
+    for (int mu = 0; mu < 4; mu++) q.k[i][mu] = sign * p[mu];
+    polarisation(p, 0, pol[i][0]);
+    polarisation(p, 1, pol[i][1]);
+  }
+  cplx ubar_s[2][4], v_s[2][4];
+  for (int s = 0; s < 2; s++) {
+    cplx u[4];
+    spinor_u(q.pt, o->mt, s, u);
+    dirac_bar(u, ubar_s[s]);
+    spinor_v(q.ptb, o->mt, s, v_s[s]);
+  }
+  double sum = 0.0;
+  cplx A[MAXPERM];
+  const int nhel = 1 << (n + 2);
+  for (int h = 0; h < nhel; h++) {
+    for (int i = 0; i < n; i++)
+      for (int mu = 0; mu < 4; mu++) q.eps[i][mu] = pol[i][(h >> i) & 1][mu]; /* real: eps* = eps */
+    const int st = (h >> n) & 1, stb = (h >> (n + 1)) & 1;
+    for (int c = 0; c < 4; c++) {
+      q.ubar[c] = ubar_s[st][c];
+      q.v[c] = v_s[stb][c];
+    }
+    all_ordered_amplitudes(&q, A);
+    cplx s = 0;
+    for (int i = 0; i < np; i++)
+      for (int j = 0; j < np; j++) s += conj(A[i]) * C[i * np + j] * A[j];
+    sum += creal(s);
+  }
+  double iden = 4.0 * 64.0;
+  for (int i = 2; i <= n - 2; i++) iden *= i; /* identical final-state gluons */
+  return sum / iden;
+}
+
+static int proc_gluons(int proc) {
+  switch (proc) {
+    case MGO_GGTT: return 2;
+    case MGO_GGTTG: return 3;
+    case MGO_GGTTGG: return 4;
+    case MGO_GGTTGGG: return 5;
+    default: return 0;
+  }
+}
+
+int mgo_npar(int proc) {
+  if (proc == MGO_EEMUMU) return 4;
+  const int n = proc_gluons(proc);
+  return n ? n + 2 : MGO_ERR_ARG;
+}
+
+/* me[i] for events i in [0, nevt): mom = [nevt][npar][4] */
+int mgo_me(int proc, const double* params, const double* mom, int64_t nevt, double* me) {
+  oparams o;
+  unpack_params(params, &o);
+  const int npar = mgo_npar(proc);
+  if (npar < 0 || nevt < 0) return MGO_ERR_ARG;
+  if (proc != MGO_EEMUMU && !colour_matrix(proc_gluons(proc))) return MGO_ERR_NOMEM;
+  for (int64_t e = 0; e < nevt; e++) {
+    const double* p = mom + (size_t)e * npar * 4;
+    me[e] = (proc == MGO_EEMUMU) ? me_eemumu(&o, p) : me_ggtt_ng(&o, proc_gluons(proc), p);
+  }
+  return MGO_OK;
+}

@@ -1,0 +1,313 @@
+"""Pins of the FP64 CPU oracle to facts outside itself.
+
+Each test ties one part of the oracle to a closed form, an identity of the
+algebra, a symmetry, or an independent brute-force evaluation, so that a
+dropped term, a wrong sign, a wrong index or a transposed operand anywhere in
+mg_oracle.c fails at least one of them:
+
+* e+e- -> mu+mu-: photon-only e^4 (1 + cos^2 theta); photon+Z helicity closed form.
+* g g -> t t~: the analytic LO result (Gamma_t = 0), and its threshold and
+  massless limits.
+* Dirac algebra, spinor and polarisation completeness (external states).
+* SU(3): Tr(T^a T^b) = delta/2, Casimir, structure constants, colour matrix
+  of g g -> t t~ exact, colour matrices real symmetric.
+* Partial amplitudes: gauge invariance (Ward identity) for every ordering and
+  every gluon with 2..5 gluons -- fixes the three- and four-gluon vertices
+  relative to the quark-gluon vertex.
+* Colour decomposition: colour-dressed recursion with explicit f^{abc},
+  summed over all colour assignments, equals A^dagger C A (2..4 gluons).
+* Full ME: Bose symmetry and Lorentz invariance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_18244_gb300.inputs import process_momenta
+
+PROC_N = {2: "g g > t t~", 3: "g g > t t~ g", 4: "g g > t t~ g g", 5: "g g > t t~ g g g"}
+SQRTS = {2: 1000.0, 3: 1200.0, 4: 1500.0, 5: 2000.0}
+
+
+def mdot(a, b):
+    return a[..., 0] * b[..., 0] - (a[..., 1:] * b[..., 1:]).sum(-1)
+
+
+# --------------------------------------------------------------------------
+# e+ e- -> mu+ mu-
+# --------------------------------------------------------------------------
+
+def _cos_e_mu(p):
+    # angle between e- (slot 1) and mu- (slot 3)
+    a, b = p[:, 1, 1:], p[:, 3, 1:]
+    return (a * b).sum(-1) / np.linalg.norm(a, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def test_eemumu_photon_only_closed_form():
+    """QED: spin-averaged |M|^2 = e^4 (1 + cos^2 theta) for massless fermions."""
+    p = process_momenta("e+ e- > mu+ mu-", 500.0, 200, 1)
+    par = O.Params(photon_only=1.0)
+    me = O.me("e+ e- > mu+ mu-", p, par)
+    e2 = 4 * math.pi / par.alpha_em_inv
+    c = _cos_e_mu(p)
+    np.testing.assert_allclose(me, e2 ** 2 * (1 + c ** 2), rtol=1e-13)
+
+
+def test_eemumu_gamma_z_helicity_closed_form():
+    """gamma+Z: (e^4/4)[(|A_LL|^2+|A_RR|^2)(1+c)^2 + (|A_LR|^2+|A_RL|^2)(1-c)^2],
+    A_ij = Q_e Q_mu + g_i g_j s / (sw^2 cw^2 (s - MZ^2 + i MZ GZ)), G_F scheme."""
+    p = process_momenta("e+ e- > mu+ mu-", 500.0, 200, 1)
+    par = O.Params()
+    me = O.me("e+ e- > mu+ mu-", p, par)
+    alpha = 1.0 / par.alpha_em_inv
+    mz2 = par.mz ** 2
+    mw2 = mz2 / 2 + math.sqrt(mz2 ** 2 / 4 - math.pi * alpha * mz2 / (math.sqrt(2) * par.gf))
+    sw2 = 1 - mw2 / mz2
+    cw2 = 1 - sw2
+    g = {"L": -0.5 + sw2, "R": sw2}
+    s = 500.0 ** 2
+    bw = s / (s - mz2 + 1j * par.mz * par.wz)
+    A = {i + j: 1.0 + g[i] * g[j] / (sw2 * cw2) * bw for i in "LR" for j in "LR"}
+    c = _cos_e_mu(p)
+    e4 = (4 * math.pi * alpha) ** 2
+    want = e4 / 4 * ((abs(A["LL"]) ** 2 + abs(A["RR"]) ** 2) * (1 + c) ** 2
+                     + (abs(A["LR"]) ** 2 + abs(A["RL"]) ** 2) * (1 - c) ** 2)
+    np.testing.assert_allclose(me, want, rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# g g -> t t~ analytic
+# --------------------------------------------------------------------------
+
+def ggtt_analytic(p, mt, alpha_s):
+    """Spin- and colour-averaged LO g g -> Q Qbar (Combridge 1979; e.g. Ellis,
+    Stirling, Webber, 'QCD and collider physics'):
+    g^4 (1/(6 t1 t2) - 3/8)(t1^2 + t2^2 + rho - rho^2/(4 t1 t2)),
+    t1 = 2 p1.p3 / s, t2 = 2 p2.p3 / s, rho = 4 m^2 / s."""
+    s = mdot(p[:, 0] + p[:, 1], p[:, 0] + p[:, 1])
+    t1 = 2 * mdot(p[:, 0], p[:, 2]) / s
+    t2 = 2 * mdot(p[:, 1], p[:, 2]) / s
+    rho = 4 * mt * mt / s
+    g4 = (4 * math.pi * alpha_s) ** 2
+    return g4 * (1 / (6 * t1 * t2) - 3 / 8) * (t1 ** 2 + t2 ** 2 + rho - rho ** 2 / (4 * t1 * t2))
+
+
+def test_ggtt_analytic_formula_limits():
+    """Self-checks of the closed form: threshold 7/48 g^4; massless gg -> qq~."""
+    g4 = (4 * math.pi * 0.118) ** 2
+    s = 1.0
+    # threshold: t1 = t2 = 1/2, rho = 1
+    t1 = t2 = 0.5
+    rho = 1.0
+    thr = g4 * (1 / (6 * t1 * t2) - 3 / 8) * (t1 ** 2 + t2 ** 2 + rho - rho ** 2 / (4 * t1 * t2))
+    assert abs(thr / g4 - 7 / 48) < 1e-15
+    # massless: (t^2+u^2)/(6tu) - 3(t^2+u^2)/(8 s^2)
+    t, u = -0.3, -0.7
+    t1, t2 = -t / s, -u / s
+    lhs = (1 / (6 * t1 * t2) - 3 / 8) * (t1 ** 2 + t2 ** 2)
+    rhs = (t * t + u * u) / (6 * t * u) - 3 * (t * t + u * u) / (8 * s * s)
+    assert abs(lhs - rhs) < 1e-15
+
+
+@pytest.mark.parametrize("mt", [173.0, 0.0])
+def test_ggtt_matches_analytic(mt):
+    p = process_momenta("g g > t t~", 1000.0, 300, 2, mt=mt)
+    par = O.Params(mt=mt, wt=0.0)
+    me = O.me("g g > t t~", p, par)
+    np.testing.assert_allclose(me, ggtt_analytic(p, mt, par.alpha_s), rtol=1e-12)
+
+
+def test_ggtt_width_is_small_effect():
+    """With Gamma_t in the t-channel propagators the result moves by O(1e-4) only."""
+    p = process_momenta("g g > t t~", 1000.0, 100, 2)
+    me = O.me("g g > t t~", p, O.Params())
+    r = me / ggtt_analytic(p, 173.0, 0.118)
+    assert np.all(np.abs(r - 1) < 1e-3)
+    assert np.any(np.abs(r - 1) > 1e-9)
+
+
+# --------------------------------------------------------------------------
+# Dirac algebra and external states
+# --------------------------------------------------------------------------
+
+G = np.diag([1.0, -1.0, -1.0, -1.0])
+
+
+def test_clifford_algebra():
+    gam = O.gamma()
+    for mu in range(4):
+        for nu in range(4):
+            ac = gam[mu] @ gam[nu] + gam[nu] @ gam[mu]
+            np.testing.assert_allclose(ac, 2 * G[mu, nu] * np.eye(4), atol=1e-15)
+        np.testing.assert_allclose(gam[4] @ gam[mu] + gam[mu] @ gam[4], 0, atol=1e-15)
+    np.testing.assert_allclose(gam[4] @ gam[4], np.eye(4), atol=1e-15)
+
+
+def _slash(p):
+    gam = O.gamma()
+    return sum(G[mu, mu] * gam[mu] * p[mu] for mu in range(4))
+
+
+@pytest.mark.parametrize("m", [173.0, 0.0])
+def test_spinor_completeness_and_dirac_equation(m):
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        k = rng.normal(size=3) * 300
+        p = np.array([math.sqrt(m * m + k @ k), *k])
+        su = sum(np.outer(O.spinor("u", p, m, s), O.spinor("ubar", p, m, s)) for s in range(2))
+        sv = sum(np.outer(O.spinor("v", p, m, s), O.spinor("vbar", p, m, s)) for s in range(2))
+        ps = _slash(p)
+        np.testing.assert_allclose(su, ps + m * np.eye(4), atol=1e-11 * p[0])
+        np.testing.assert_allclose(sv, ps - m * np.eye(4), atol=1e-11 * p[0])
+        for s in range(2):
+            np.testing.assert_allclose((ps - m * np.eye(4)) @ O.spinor("u", p, m, s), 0, atol=1e-10 * p[0])
+            np.testing.assert_allclose((ps + m * np.eye(4)) @ O.spinor("v", p, m, s), 0, atol=1e-10 * p[0])
+
+
+def test_polarisation_transverse_complete():
+    rng = np.random.default_rng(2)
+    dirs = [rng.normal(size=3) for _ in range(5)] + [np.array([0, 0, 1.0]), np.array([0, 0, -1.0])]
+    for d in dirs:
+        k = np.array([np.linalg.norm(d), *d]) * 100
+        e = np.array([O.polarisation(k, w) for w in range(2)])
+        assert np.allclose(e[:, 0], 0)
+        np.testing.assert_allclose(e[:, 1:] @ k[1:], 0, atol=1e-12)
+        np.testing.assert_allclose(e[:, 1:] @ e[:, 1:].T, np.eye(2), atol=1e-14)
+        kh = k[1:] / np.linalg.norm(k[1:])
+        np.testing.assert_allclose(e[:, 1:].T @ e[:, 1:], np.eye(3) - np.outer(kh, kh), atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# SU(3) colour algebra
+# --------------------------------------------------------------------------
+
+def test_gell_mann_algebra():
+    T = O.generators()
+    tr = np.einsum("aij,bji->ab", T, T)
+    np.testing.assert_allclose(tr, 0.5 * np.eye(8), atol=1e-15)
+    np.testing.assert_allclose(np.einsum("aij,ajk->ik", T, T), 4 / 3 * np.eye(3), atol=1e-15)
+    for a in range(8):
+        np.testing.assert_allclose(T[a], T[a].conj().T, atol=0)
+        assert abs(np.trace(T[a])) < 1e-15
+    f = O.fabc()
+    assert abs(f[0, 1, 2] - 1.0) < 1e-14                  # f^{123} = 1
+    assert abs(f[3, 4, 7] - math.sqrt(3) / 2) < 1e-14      # f^{458} = sqrt(3)/2
+    np.testing.assert_allclose(f, -np.transpose(f, (1, 0, 2)), atol=1e-15)
+    np.testing.assert_allclose(f, np.transpose(f, (1, 2, 0)), atol=1e-15)
+    # [T^a, T^b] = i f^{abc} T^c
+    comm = np.einsum("aij,bjk->abik", T, T) - np.einsum("bij,ajk->abik", T, T)
+    np.testing.assert_allclose(comm, 1j * np.einsum("abc,cik->abik", f, T), atol=1e-15)
+    # adjoint Casimir: f^{acd} f^{bcd} = 3 delta^{ab}
+    np.testing.assert_allclose(np.einsum("acd,bcd->ab", f, f), 3 * np.eye(8), atol=1e-13)
+
+
+def test_colour_matrix_ggtt_exact():
+    C = O.colour_matrix(2)
+    np.testing.assert_allclose(C, [[16 / 3, -2 / 3], [-2 / 3, 16 / 3]], atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_colour_matrix_real_symmetric(n):
+    C = O.colour_matrix(n)
+    assert np.max(np.abs(C.imag)) < 1e-13
+    np.testing.assert_allclose(C.real, C.real.T, atol=1e-13)
+    # diagonal: sum over a of Tr(T^a1..T^an T^an..T^a1) = N C_F^n
+    np.testing.assert_allclose(np.diag(C.real), 3 * (4 / 3) ** n, rtol=1e-12)
+    # positive semi-definite (a sum of |.|^2)
+    assert np.linalg.eigvalsh(C.real).min() > -1e-10
+
+
+# --------------------------------------------------------------------------
+# Partial amplitudes: Ward identities, colour decomposition
+# --------------------------------------------------------------------------
+
+def _qline_states(n, seed, which=(0, 0), pol=0):
+    p = process_momenta(PROC_N[n], SQRTS[n], 1, seed)[0]
+    slots = [0, 1] + list(range(4, n + 2))
+    kin = np.array([p[s] if s < 2 else -p[s] for s in slots])
+    eps = np.array([O.polarisation(p[s], (pol >> i) & 1) for i, s in enumerate(slots)], dtype=complex)
+    ub = O.spinor("ubar", p[2], 173.0, which[0])
+    v = O.spinor("v", p[3], 173.0, which[1])
+    return p, kin, eps, ub, v
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+@pytest.mark.parametrize("seed", [7, 8])
+def test_ward_identity_every_ordering(n, seed):
+    """eps_i -> k_i annihilates every colour-ordered amplitude (Gamma_t = 0)."""
+    par = O.Params(wt=0.0)
+    p, kin, eps, ub, v = _qline_states(n, seed, which=(seed & 1, 1), pol=seed)
+    A = O.ordered_amps(n, kin, eps, p[2], ub, p[3], v, par)
+    scale = np.max(np.abs(A))
+    for i in range(n):
+        e2 = eps.copy()
+        e2[i] = kin[i]
+        W = O.ordered_amps(n, kin, e2, p[2], ub, p[3], v, par)
+        # k_i carries the scale of an energy: normalise by it
+        assert np.max(np.abs(W)) / kin[i][0] < 1e-10 * scale
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_colour_dressed_recursion_equals_colour_ordered(n):
+    """Explicit-colour recursion (P&S vertices with f^{abc}) summed over every
+    colour assignment equals A^dagger C A from the colour-ordered recursion."""
+    par = O.Params()
+    for seed, pol in ((3, 0), (4, 5)):
+        p, kin, eps, ub, v = _qline_states(n, seed, which=(0, 1), pol=pol)
+        d = O.dressed_colour_sum(n, kin, eps, p[2], ub, p[3], v, par)
+        o = O.ordered_colour_sum(n, kin, eps, p[2], ub, p[3], v, par)
+        assert abs(d / o - 1) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Full ME: symmetries
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,nevt", [(2, 20), (3, 10), (4, 6), (5, 1)])
+def test_bose_symmetry(n, nevt):
+    proc = PROC_N[n]
+    p = process_momenta(proc, SQRTS[n], nevt, 21)
+    me = O.me(proc, p)
+    # swap the two initial gluons
+    q = p.copy()
+    q[:, [0, 1]] = q[:, [1, 0]]
+    np.testing.assert_allclose(O.me(proc, q), me, rtol=1e-12)
+    if n >= 4:
+        q = p.copy()
+        q[:, [4, n + 1]] = q[:, [n + 1, 4]]
+        np.testing.assert_allclose(O.me(proc, q), me, rtol=1e-12)
+
+
+def _boost_rotate(p, beta, axis, angle):
+    b = np.asarray(beta, dtype=float)
+    b2 = b @ b
+    gam = 1 / math.sqrt(1 - b2)
+    L = np.eye(4)
+    L[0, 0] = gam
+    L[0, 1:] = L[1:, 0] = gam * b
+    L[1:, 1:] += (gam - 1) * np.outer(b, b) / b2
+    ax = np.asarray(axis, dtype=float) / np.linalg.norm(axis)
+    K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    R = np.eye(4)
+    R[1:, 1:] = np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+    return p @ (L @ R).T
+
+
+@pytest.mark.parametrize("n,nevt", [(2, 20), (3, 8), (4, 4), (5, 1)])
+def test_lorentz_invariance(n, nevt):
+    """Boost + rotation of every momentum leaves the spin/colour sum unchanged
+    (Gamma_t = 0, so the amplitudes are gauge invariant)."""
+    proc = PROC_N[n]
+    par = O.Params(wt=0.0)
+    p = process_momenta(proc, SQRTS[n], nevt, 31)
+    me = O.me(proc, p, par)
+    q = _boost_rotate(p, [0.3, -0.2, 0.5], [1, 2, 3], 0.7)
+    np.testing.assert_allclose(O.me(proc, q, par), me, rtol=1e-11)
+
+
+def test_eemumu_lorentz_invariance_with_z_width():
+    p = process_momenta("e+ e- > mu+ mu-", 500.0, 20, 41)
+    me = O.me("e+ e- > mu+ mu-", p)
+    q = _boost_rotate(p, [0.1, 0.4, -0.3], [0, 1, 1], 1.1)
+    np.testing.assert_allclose(O.me("e+ e- > mu+ mu-", q), me, rtol=1e-12)
