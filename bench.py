@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark: g g -> t t~ g g matrix elements per second on one GB300.
+
+Workload (the paper's headline process, Tables 1-2): 524288 RAMBO events at
+sqrt(s) = 1.5 TeV, Philox seed 3, mt = 173 GeV, Gamma_t = 1.4915 GeV,
+alpha_s = 0.118.  A step is one mg_sigma call over the whole batch (steps
+A1-A6: momentum staging, wavefunctions, diagrams, colour sum, helicity sum),
+with the good-helicity set-up (A0) done once before timing.  The headline
+value is the mixed-precision path; the FP64 path on the same events, the
+mixed-vs-FP64 accuracy, an end-to-end number through host buffers, the
+roofline of the dominant kernel and the FP64 CPU oracle's throughput on a
+bounded sample are reported beside it.  --serve adds the continuous-batching
+request loop (Poisson arrivals, four processes) with p50/p99 latency.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+Multi-GPU (torchrun): events are independent, so each rank evaluates its own
+batch (event offsets rank * nevt) with no data-path collective: weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PROC = "g g > t t~ g g"
+SQRTS = 1500.0
+SEED = 3
+NEVT = 524288
+METRIC = "gg→tt̄gg MEs/s on 1 GB300, FP64 vs mixed (≤1e-5 rel err); serve p50/p99 ms"
+L2_FLUSH_BYTES = 256 << 20
+
+SERVE_PROCS = {  # process -> sqrt(s)
+    "e+ e- > mu+ mu-": 500.0,
+    "g g > t t~": 1000.0,
+    "g g > t t~ g g": 1500.0,
+    "g g > t t~ g g g": 2000.0,
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during timing."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_flops(tag: str) -> dict:
+    with open(os.path.join(ROOT, "paper_2303_18244_gb300", "flops.json")) as f:
+        return json.load(f)[tag]
+
+
+def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: float = 12.0):
+    """FP64 oracle on the host cores over a bounded sample: (MEs/s, cores, n)."""
+    import oracle as O
+    from paper_2303_18244_gb300.inputs import process_momenta
+    cores = os.cpu_count() or 1
+    O.me(proc, process_momenta(proc, sqrts, cores, seed, first_event))  # colour matrix, warm
+    n = cores
+    best = None
+    while True:
+        p = process_momenta(proc, sqrts, n, seed, first_event)
+        t = time.perf_counter()
+        O.me(proc, p, threads=cores)
+        dt = time.perf_counter() - t
+        best = (n / dt, cores, n, dt)
+        if dt >= budget_s / 4 or n >= 1 << 20:
+            break
+        n = int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3))))
+    return best
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2303_18244_gb300.inputs import process_momenta  # noqa: F401
+    vals = []
+    info = None
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        time_oracle(PROC, SQRTS, SEED, 0, budget_s=2.0)
+    for _ in range(args.steps):
+        v, cores, n, dt = time_oracle(PROC, SQRTS, SEED, 0, budget_s=8.0)
+        vals.append(v)
+        info = (cores, n)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MEs/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * info[1] / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (RAMBO flat phase space, Philox seed 3)",
+            "config": {"workload": f"{PROC}, {NEVT} events at sqrt(s)={SQRTS:.0f} GeV (sample of {info[1]})",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "MEs/s", "cores": info[0], "kind": "oracle",
+                             "sample": f"{info[1]} events of the workload per step"},
+            "e2e": {"value": v, "unit": "MEs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--nevt", type=int, default=NEVT)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--serve", action="store_true", help="also run the serving benchmark")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2303_18244_gb300 import mg
+    from paper_2303_18244_gb300.inputs import process_momenta
+
+    nevt = args.nevt
+    first = rank * nevt
+    p = process_momenta(PROC, SQRTS, nevt, SEED, first_event=first)
+    calib = process_momenta(PROC, SQRTS, 1024, SEED + 1000)
+    mom = torch.from_numpy(p).cuda()
+    out = torch.empty(nevt, dtype=torch.float64, device="cuda")
+    out64 = torch.empty(nevt, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    hmix = mg.Process(PROC, precision=mg.MG_MIXED)
+    h64 = mg.Process(PROC, precision=mg.MG_FP64)
+    ngood, _ = mg.good_helicities(hmix, torch.from_numpy(calib).cuda())
+    mg.good_helicities(h64, torch.from_numpy(calib).cuda())
+
+    def timed(h, o, steps, warmup):
+        for _ in range(warmup):
+            mg.sigma(h, mom, o, stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        per = []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps (inputs are smaller than L2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mg.sigma(h, mom, o, stream)
+            e1.record(stream)
+            per.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in per]
+        if world > 1:
+            torch.distributed.barrier()
+        return ms
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_mix = timed(hmix, out, args.steps, args.warmup)
+    clk = clocks.stop()
+    assert mg.process_status(hmix) == 0
+    ms_64 = timed(h64, out64, args.fp64_steps, 1)
+    assert mg.process_status(h64) == 0
+
+    t_mix = sum(ms_mix)
+    t_64 = sum(ms_64) / len(ms_64)
+    if world > 1:
+        t = torch.tensor([t_mix, t_64], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_mix, t_64 = t.tolist()
+    value = world * nevt * args.steps / (t_mix * 1e-3)
+    value64 = world * nevt / (t_64 * 1e-3)
+
+    # accuracy of the mixed path against the FP64 GPU path (itself held to the
+    # FP64 oracle at <= 1e-12 by the parity tests) on every event of the batch
+    a = out.cpu().numpy()
+    b = out64.cpu().numpy()
+    rel = np.abs(a - b) / np.abs(b)
+
+    # end to end through the C ABI from pinned host buffers
+    hp = torch.from_numpy(p).pin_memory()
+    ho = torch.empty(nevt, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        mg.sigma_host(hmix, hp, ho, stream)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        mg.sigma_host(hmix, hp, ho, stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = statistics.median(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = t.item()
+
+    fl = load_flops("ggttgg")
+    flops_evt = ngood * (fl["amp_flops_per_hel"] + fl["colour_dense_flops_per_hel"])
+    kernel_ms = t_mix / args.steps
+    achieved = flops_evt * nevt / (kernel_ms * 1e-3) / 1e12
+    peak32 = mg.diag_fma_peak(0) / 1e3
+    peak64 = mg.diag_fma_peak(1) / 1e3
+    achieved64 = flops_evt * nevt / (t_64 * 1e-3) / 1e12
+
+    res = {
+        "metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_mix / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 denominators and helicity sum)",
+        "data": "synthetic (RAMBO flat phase space, Philox seed 3)",
+        "config": {"workload": f"{PROC}, {nevt} events/GPU at sqrt(s)={SQRTS:.0f} GeV, mixed precision",
+                   "good_helicities": ngood, "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"events sharded, {world} rank(s), no collective"},
+        "fp64": {"value": value64, "unit": "MEs/s", "ms_per_step": t_64,
+                 "roofline": {"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
+                              "frac": achieved64 / peak64, "peak_source": "measured FP64 FMA loop (mg_diag)"}},
+        "accuracy_mixed_vs_fp64": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
+                                   "max": float(rel.max()), "events": nevt},
+        "e2e": {"value": world * nevt / (e2e_t * 1e-3), "unit": "MEs/s",
+                "h2d_bytes_per_step": int(p.nbytes), "d2h_bytes_per_step": int(nevt * 8)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
+                     "frac": achieved / peak32, "traffic": None,
+                     "kernel": "sigma_kernel<ggttgg, float>",
+                     "flops_per_event": flops_evt,
+                     "peak_source": "measured FP32 FMA loop (mg_diag), burst"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, n, dt = time_oracle(PROC, SQRTS, SEED, first)
+        res["cpu_baseline"] = {"value": v, "unit": "MEs/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{n} events of the workload ({dt:.1f} s wall)"}
+    if args.serve:
+        res["serve"] = serve_bench(args, mg, process_momenta)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def serve_bench(args, mg, process_momenta):
+    """Poisson arrivals (mean gap 2 ms) of requests drawn uniformly from four
+    processes, log-uniform 256..65536 events each (Philox seed 5 drives the
+    choices), served by the continuous-batching loop; p50/p99 latency."""
+    from paper_2303_18244_gb300.inputs import uniforms
+    out = {}
+    for prec_name, prec in (("mixed", mg.MG_MIXED), ("fp64", mg.MG_FP64)):
+        handles = {p: mg.Process(p, precision=prec) for p in SERVE_PROCS}
+        u = uniforms(5, 0, args.serve_requests, 1)[:, 0, :]
+        reqs = []
+        for i in range(args.serve_requests):
+            proc = list(SERVE_PROCS)[min(3, int(u[i, 0] * 4))]
+            n = int(round(math.exp(math.log(256) + u[i, 1] * (math.log(65536) - math.log(256)))))
+            gap = -2e-3 * math.log(u[i, 2])
+            mom = process_momenta(proc, SERVE_PROCS[proc], n, 5, first_event=i * 65536)
+            reqs.append((proc, n, gap, mom, np.empty(n)))
+        srv = mg.Server()
+        ids = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for proc, n, gap, mom, me in reqs:
+            t_next += gap
+            while time.perf_counter() < t_next:
+                pass
+            ids.append(srv.submit(handles[proc], mom, me))
+        lat = []
+        tot = 0
+        for rid, (proc, n, *_rest) in zip(ids, reqs):
+            while True:
+                rc, st = srv.poll(rid, 1000000)
+                if rc == 0:
+                    break
+            lat.append(st.latency_us / 1e3)
+            tot += n
+        wall = time.perf_counter() - t0
+        srv.close()
+        out[prec_name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "MEs_per_s": tot / wall, "requests": len(reqs), "events": tot}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+// mg_kernels.cuh -- kernel templates of the matrix-element hot path.
+//
+// One event per thread, lockstep across the warp (paper Sect. 1: data
+// parallelism with lockstep processing over the events of a batch):
+//   A1  the CTA's momenta tile (NT events x NPAR x 4 doubles, contiguous) is
+//       copied global -> shared by the TMA engine (cp.async.bulk, completion
+//       on an mbarrier with a bounded wait);
+//   A2  per event, once, in FP64: external-state ingredients and every
+//       propagator coefficient -g/P^2, -g/(P^2 - m^2 + i m Gamma) -- these
+//       depend on the momenta only, so they are hoisted out of the helicity
+//       loop and kept in a per-thread shared-memory slab [slot][thread];
+//   A3-A4  per good helicity (uniform across the CTA): wavefunctions,
+//       off-shell currents and amplitudes diagram by diagram, accumulated
+//       into the colour flows (generated straight-line code);
+//   A5  colour quadratic form J^dagger C J (FP64 FMA in the FP64 path; on
+//       the tensor cores in the mixed path, see mg_colour_tc.cuh);
+//   A6  helicity sum in FP64, normalised by 1/(IDEN * CDEN), one store.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg_vertices.cuh"
+
+namespace mg {
+
+struct KParams {
+  double v[8];
+};
+
+// status bits written by kernels
+enum : unsigned { ST_TMA_TIMEOUT = 1u, ST_MMA_TIMEOUT = 2u };
+
+// ---------------------------------------------------------------------------
+// mbarrier / bulk-copy primitives (PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after max_iter polls (each poll may itself suspend
+// for a short hardware-defined time).  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
+  for (uint32_t i = 0; i < max_iter; i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// global -> shared bulk copy (TMA engine), completion counted on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr uint32_t WAIT_POLLS = 1u << 22;
+
+// ---------------------------------------------------------------------------
+// shared-memory layout: [mbarriers 128 B][momenta tile][per-thread slab]
+// ---------------------------------------------------------------------------
+template <class P, typename R, int NT>
+struct Layout {
+  static constexpr size_t bar_bytes = 128;
+  static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
+  static constexpr size_t slab_bytes = size_t(NT) * P::NSLOT * sizeof(R);
+  static constexpr size_t slab_off = bar_bytes + ((stage_bytes + 127) / 128) * 128;
+  static constexpr size_t base_bytes = slab_off + ((slab_bytes + 127) / 128) * 128;
+};
+
+// A1 + A2: stage the tile, run the per-event FP64 set-up into the slab.
+// Returns the number of valid events in the tile, or -1 after a timed-out copy.
+template <class P, typename R, int NT>
+__device__ __forceinline__ int load_and_prepare(unsigned char* smem, const double* __restrict__ mom, long long nevt,
+                                                const KParams& kp, unsigned* status) {
+  using LY = Layout<P, R, NT>;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  double* stage = reinterpret_cast<double*>(smem + LY::bar_bytes);
+  R* slab = reinterpret_cast<R*>(smem + LY::slab_off);
+  const int tid = threadIdx.x;
+  const long long e0 = (long long)blockIdx.x * NT;
+  const long long rem = nevt - e0;
+  const int nvalid = rem < NT ? (int)rem : NT;
+  const uint32_t bytes = (uint32_t)nvalid * P::NPAR * 4 * sizeof(double);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(stage, mom + e0 * P::NPAR * 4, bytes, bar);
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0, WAIT_POLLS)) {
+    // the copy did not complete: flag it, wait once more (bounded) so that no
+    // copy is left in flight into this CTA's shared memory, and give up
+    if (tid == 0) atomicOr(status, ST_TMA_TIMEOUT);
+    mbar_wait_bounded(bar, 0, WAIT_POLLS);
+    return -1;
+  }
+  const int le = tid < nvalid ? tid : nvalid - 1;  // ragged tail: repeat a valid event
+  P::template prepare<R>(stage + le * P::NPAR * 4, kp.v, slab + tid, NT);
+  return nvalid;
+}
+
+// ---------------------------------------------------------------------------
+// |M|^2 with the CUDA-core colour sum (FP64 path; small processes in mixed)
+// ---------------------------------------------------------------------------
+template <class P, typename R, int NT>
+__global__ void __launch_bounds__(NT) sigma_kernel(const double* __restrict__ mom, long long nevt,
+                                                   double* __restrict__ me, const int* __restrict__ hels,
+                                                   int nhel, KParams kp, unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using LY = Layout<P, R, NT>;
+  const int nvalid = load_and_prepare<P, R, NT>(smem, mom, nevt, kp, status);
+  if (nvalid < 0) return;
+  const R* ev = reinterpret_cast<const R*>(smem + LY::slab_off) + threadIdx.x;
+  double acc = 0.0;
+  for (int ih = 0; ih < nhel; ih++) {
+    const int h = __ldg(hels + ih);
+    cx<R> jamp[P::NCOL];
+    P::template amplitudes<R>(ev, NT, h, kp.v, jamp);
+    acc += (double)P::template colour_quadratic<R>(jamp);
+  }
+  if ((int)threadIdx.x < nvalid) {
+    constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+    me[(long long)blockIdx.x * NT + threadIdx.x] = acc * norm;
+  }
+}
+
+// Per-helicity |M_h|^2 / IDEN for every helicity, FP64 (helicity filter).
+template <class P, int NT>
+__global__ void __launch_bounds__(NT) helicity_kernel(const double* __restrict__ mom, long long nevt,
+                                                      double* __restrict__ out, KParams kp,
+                                                      unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using LY = Layout<P, double, NT>;
+  const int nvalid = load_and_prepare<P, double, NT>(smem, mom, nevt, kp, status);
+  if (nvalid < 0) return;
+  const double* ev = reinterpret_cast<const double*>(smem + LY::slab_off) + threadIdx.x;
+  const long long e = (long long)blockIdx.x * NT + threadIdx.x;
+  constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+  for (int h = 0; h < P::NHEL; h++) {
+    cx<double> jamp[P::NCOL];
+    P::template amplitudes<double>(ev, NT, h, kp.v, jamp);
+    const double v = P::template colour_quadratic<double>(jamp) * norm;
+    if ((int)threadIdx.x < nvalid) out[e * P::NHEL + h] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+struct LaunchArgs {
+  const double* mom;
+  long long nevt;
+  double* out;
+  const int* hels;
+  int nhel;
+  KParams kp;
+  unsigned* status;
+  cudaStream_t stream;
+};
+
+template <class K>
+inline cudaError_t set_smem_attr(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class P, typename R, int NT>
+int launch_sigma(const LaunchArgs& a) {
+  constexpr size_t smem = Layout<P, R, NT>::base_bytes;
+  static const cudaError_t attr = set_smem_attr(sigma_kernel<P, R, NT>, smem);
+  if (attr != cudaSuccess) return -4;
+  if (a.nevt <= 0) return 0;  // attribute set-up only
+  const long long grid = (a.nevt + NT - 1) / NT;
+  sigma_kernel<P, R, NT><<<(unsigned)grid, NT, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels, a.nhel, a.kp,
+                                                                  a.status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <class P, int NT>
+int launch_helicities(const LaunchArgs& a) {
+  constexpr size_t smem = Layout<P, double, NT>::base_bytes;
+  static const cudaError_t attr = set_smem_attr(helicity_kernel<P, NT>, smem);
+  if (attr != cudaSuccess) return -4;
+  if (a.nevt <= 0) return 0;  // attribute set-up only
+  const long long grid = (a.nevt + NT - 1) / NT;
+  helicity_kernel<P, NT><<<(unsigned)grid, NT, smem, a.stream>>>(a.mom, a.nevt, a.out, a.kp, a.status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+// process descriptor exported by each generated translation unit
+struct ProcDesc {
+  const char* name;
+  const char* tag;
+  int npar, nhel, ncol, ndiag, namp;
+  double iden;
+  int cden;
+  const int* knum;  // [ncol * ncol], C = knum / cden
+  int (*sigma_fp64)(const LaunchArgs&);
+  int (*sigma_mixed)(const LaunchArgs&);
+  int (*helicities)(const LaunchArgs&);
+};
+
+}  // namespace mg

@@ -1,0 +1,32 @@
+// mg_runtime_internal.h -- the process handle shared by the runtime and the server.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "mg.h"
+#include "mg_kernels.cuh"
+
+struct mg_process {
+  const mg::ProcDesc* d = nullptr;
+  mg_params par{};
+  mg::KParams kp{};
+  int device = 0;
+  int* d_hels = nullptr;            // good helicity indices [n_good] (device)
+  std::vector<int*> old_hels;       // superseded lists, freed at destroy
+  int n_good = 0;
+  unsigned hel_version = 0;         // bumped when the helicity list changes
+  std::vector<uint8_t> mask;
+  unsigned* d_status = nullptr;     // device status word (bounded-wait timeouts)
+  std::mutex lock;
+  // workspace of mg_sigma_host
+  std::mutex ws_lock;
+  double* d_mom = nullptr;
+  double* d_me = nullptr;
+  int64_t cap = 0;
+};
+
+// stream-ordered launch of the handle's sigma kernel (no argument checks)
+int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, cudaStream_t stream);

@@ -1,0 +1,417 @@
+// mg_vertices.cuh -- device library of helicity wavefunctions and vertices.
+//
+// Helicity amplitudes in the spirit of HELAS (Murayama, Watanabe, Hagiwara
+// 1992; cited by the paper in Sect. 1 for its Feynman-diagram method), written
+// here from the Feynman rules in the Weyl (chiral) representation:
+//   gamma^mu = [[0, sigma^mu], [sigmabar^mu, 0]],  psi = (psi_L, psi_R),
+//   sigma^mu = (1, sigma^i), sigmabar^mu = (1, -sigma^i),  metric (+,-,-,-).
+// A vector J gives Jslash = [[0, X], [Y, 0]] with
+//   X = sigma.J    = [[J0-J3, -J1+iJ2], [-J1-iJ2, J0+J3]]
+//   Y = sigmabar.J = [[J0+J3,  J1-iJ2], [ J1+iJ2, J0-J3]].
+// Row spinors (ubar-like, 4 components) multiply from the left, column
+// spinors (u/v-like) from the right.  Everything is templated on the real
+// type R (double for the FP64 path, float for the mixed path).
+#pragma once
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#endif
+#include <math.h>
+#include <stdint.h>
+
+namespace mg {
+
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> C(R a, R b) {
+  return cx<R>{a, b};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) {
+  return {a.re + b.re, a.im + b.im};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) {
+  return {a.re - b.re, a.im - b.im};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) {
+  return {-a.re, -a.im};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) {
+  return {s * a.re, s * a.im};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> conj(cx<R> a) {
+  return {a.re, -a.im};
+}
+// i * a
+template <typename R>
+__device__ __forceinline__ cx<R> mul_i(cx<R> a) {
+  return {-a.im, a.re};
+}
+// a + b*c (complex)
+template <typename R>
+__device__ __forceinline__ cx<R> fma(cx<R> b, cx<R> c, cx<R> a) {
+  return {a.re + b.re * c.re - b.im * c.im, a.im + b.re * c.im + b.im * c.re};
+}
+// a + s*b (real s)
+template <typename R>
+__device__ __forceinline__ cx<R> fma(R s, cx<R> b, cx<R> a) {
+  return {a.re + s * b.re, a.im + s * b.im};
+}
+
+template <typename R>
+__device__ __forceinline__ R fmaf_t(R a, R b, R c) {
+  return a * b + c;
+}
+
+template <typename R>
+struct V4 {  // contravariant vector current
+  cx<R> c[4];
+};
+template <typename R>
+struct Sp {  // Weyl-basis 4-spinor (row or column)
+  cx<R> c[4];
+};
+
+// Minkowski products
+template <typename R>
+__device__ __forceinline__ cx<R> dot(const V4<R>& a, const V4<R>& b) {
+  cx<R> s = a.c[0] * b.c[0];
+  s = s - a.c[1] * b.c[1];
+  s = s - a.c[2] * b.c[2];
+  s = s - a.c[3] * b.c[3];
+  return s;
+}
+template <typename R>
+__device__ __forceinline__ cx<R> dot(const R k[4], const V4<R>& b) {
+  return {k[0] * b.c[0].re - k[1] * b.c[1].re - k[2] * b.c[2].re - k[3] * b.c[3].re,
+          k[0] * b.c[0].im - k[1] * b.c[1].im - k[2] * b.c[2].im - k[3] * b.c[3].im};
+}
+
+// ---------------------------------------------------------------------------
+// external wavefunctions (per helicity, from per-event ingredients)
+// ---------------------------------------------------------------------------
+
+// Massless vector of helicity lam = +-1; e1s, e2s = e1/sqrt2, e2/sqrt2 with
+// e1 = (cos th cos ph, cos th sin ph, -sin th), e2 = (-sin ph, cos ph, 0):
+//   incoming eps = -lam e1s - i e2s,  outgoing eps* = -lam e1s + i e2s.
+template <typename R>
+__device__ __forceinline__ V4<R> ext_vector(const R e1s[3], const R e2s[3], R lam, bool outgoing) {
+  V4<R> w;
+  const R s = outgoing ? R(1) : R(-1);
+  w.c[0] = {R(0), R(0)};
+  for (int i = 0; i < 3; i++) w.c[i + 1] = {-lam * e1s[i], s * e2s[i]};
+  return w;
+}
+
+// Two-component helicity eigenstates along phat: chi+ = (a, b), chi- = (-b*, a).
+// Fermion ingredients per event: a (real), b (complex), om_m = sqrt(E-|p|),
+// om_p = sqrt(E+|p|).
+template <typename R>
+struct FermIngr {
+  R a, bre, bim, om_m, om_p;
+};
+
+template <typename R>
+__device__ __forceinline__ void chi(const FermIngr<R>& f, int lam, cx<R>& c0, cx<R>& c1) {
+  if (lam > 0) {
+    c0 = {f.a, R(0)};
+    c1 = {f.bre, f.bim};
+  } else {
+    c0 = {-f.bre, f.bim};
+    c1 = {f.a, R(0)};
+  }
+}
+
+// outgoing fermion: ubar(lam) = ( om_lam chi_lam^*, om_{-lam} chi_lam^* )
+template <typename R>
+__device__ __forceinline__ Sp<R> ext_ubar(const FermIngr<R>& f, int lam) {
+  cx<R> c0, c1;
+  chi(f, lam, c0, c1);
+  const R wl = lam > 0 ? f.om_p : f.om_m;
+  const R wm = lam > 0 ? f.om_m : f.om_p;
+  Sp<R> s;
+  s.c[0] = wl * conj(c0);
+  s.c[1] = wl * conj(c1);
+  s.c[2] = wm * conj(c0);
+  s.c[3] = wm * conj(c1);
+  return s;
+}
+// outgoing antifermion: v(lam) = ( om_lam chi_{-lam} ; -om_{-lam} chi_{-lam} )
+template <typename R>
+__device__ __forceinline__ Sp<R> ext_v(const FermIngr<R>& f, int lam) {
+  cx<R> c0, c1;
+  chi(f, -lam, c0, c1);
+  const R wl = lam > 0 ? f.om_p : f.om_m;
+  const R wm = lam > 0 ? f.om_m : f.om_p;
+  Sp<R> s;
+  s.c[0] = wl * c0;
+  s.c[1] = wl * c1;
+  s.c[2] = -wm * c0;
+  s.c[3] = -wm * c1;
+  return s;
+}
+// incoming fermion: u(lam) = ( om_{-lam} chi_lam ; om_lam chi_lam )
+template <typename R>
+__device__ __forceinline__ Sp<R> ext_u(const FermIngr<R>& f, int lam) {
+  cx<R> c0, c1;
+  chi(f, lam, c0, c1);
+  const R wl = lam > 0 ? f.om_p : f.om_m;
+  const R wm = lam > 0 ? f.om_m : f.om_p;
+  Sp<R> s;
+  s.c[0] = wm * c0;
+  s.c[1] = wm * c1;
+  s.c[2] = wl * c0;
+  s.c[3] = wl * c1;
+  return s;
+}
+// incoming antifermion: vbar(lam) = ( -om_{-lam} chi_{-lam}^*, om_lam chi_{-lam}^* )
+template <typename R>
+__device__ __forceinline__ Sp<R> ext_vbar(const FermIngr<R>& f, int lam) {
+  cx<R> c0, c1;
+  chi(f, -lam, c0, c1);
+  const R wl = lam > 0 ? f.om_p : f.om_m;
+  const R wm = lam > 0 ? f.om_m : f.om_p;
+  Sp<R> s;
+  s.c[0] = -wm * conj(c0);
+  s.c[1] = -wm * conj(c1);
+  s.c[2] = wl * conj(c0);
+  s.c[3] = wl * conj(c1);
+  return s;
+}
+
+// Per-event fermion ingredients in FP64 (stable forms: E - |p| = m^2/(E+|p|),
+// |p| + pz = pT^2/(|p| - pz) for pz < 0).
+__device__ __forceinline__ void fermion_ingredients(const double p[4], double m, double out[5]) {
+  const double pt2 = p[1] * p[1] + p[2] * p[2];
+  const double P = sqrt(pt2 + p[3] * p[3]);
+  const double E = p[0];
+  const double om_p = sqrt(E + P);
+  const double om_m = (m == 0.0) ? 0.0 : sqrt(m * m / (E + P));
+  const double s = (p[3] >= 0.0) ? (P + p[3]) : (pt2 / (P - p[3]));
+  double a, bre, bim;
+  if (s > 0.0) {
+    a = sqrt(s / (2.0 * P));
+    const double r = 1.0 / sqrt(2.0 * P * s);
+    bre = p[1] * r;
+    bim = p[2] * r;
+  } else {
+    a = 0.0;
+    bre = 1.0;
+    bim = 0.0;
+  }
+  out[0] = a;
+  out[1] = bre;
+  out[2] = bim;
+  out[3] = om_m;
+  out[4] = om_p;
+}
+
+// Per-event transverse basis e1/sqrt2, e2/sqrt2 of a massless vector (FP64).
+__device__ __forceinline__ void vector_basis(const double k[4], double out[6]) {
+  const double pt2 = k[1] * k[1] + k[2] * k[2];
+  const double P = sqrt(pt2 + k[3] * k[3]);
+  double cph, sph, cth, sth;
+  if (pt2 > 0.0) {
+    const double pt = sqrt(pt2);
+    cph = k[1] / pt;
+    sph = k[2] / pt;
+    cth = k[3] / P;
+    sth = pt / P;
+  } else {
+    cph = 1.0;
+    sph = 0.0;
+    cth = (k[3] >= 0.0) ? 1.0 : -1.0;
+    sth = 0.0;
+  }
+  const double r = 0.70710678118654752440;
+  out[0] = r * cth * cph;
+  out[1] = r * cth * sph;
+  out[2] = -r * sth;
+  out[3] = -r * sph;
+  out[4] = r * cph;
+  out[5] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// vertices
+// ---------------------------------------------------------------------------
+
+// X = sigma.J, Y = sigmabar.J for a complex vector J (2x2 each, row-major)
+template <typename R>
+__device__ __forceinline__ void sigma_blocks(const V4<R>& J, cx<R> X[4], cx<R> Y[4]) {
+  const cx<R> iJ2 = mul_i(J.c[2]);
+  X[0] = J.c[0] - J.c[3];
+  X[1] = iJ2 - J.c[1];
+  X[2] = -(J.c[1] + iJ2);
+  X[3] = J.c[0] + J.c[3];
+  Y[0] = X[3];
+  Y[1] = J.c[1] - iJ2;
+  Y[2] = J.c[1] + iJ2;
+  Y[3] = X[0];
+}
+// same for a real momentum Q
+template <typename R>
+__device__ __forceinline__ void sigma_blocks(const R Q[4], cx<R> X[4], cx<R> Y[4]) {
+  X[0] = {Q[0] - Q[3], R(0)};
+  X[1] = {-Q[1], Q[2]};
+  X[2] = {-Q[1], -Q[2]};
+  X[3] = {Q[0] + Q[3], R(0)};
+  Y[0] = X[3];
+  Y[1] = {Q[1], -Q[2]};
+  Y[2] = {Q[1], Q[2]};
+  Y[3] = X[0];
+}
+// row (r0, r1) times 2x2 M
+template <typename R>
+__device__ __forceinline__ void rowmul(cx<R> r0, cx<R> r1, const cx<R> M[4], cx<R>& o0, cx<R>& o1) {
+  o0 = r0 * M[0] + r1 * M[2];
+  o1 = r0 * M[1] + r1 * M[3];
+}
+// 2x2 M times column (c0, c1)
+template <typename R>
+__device__ __forceinline__ void mulcol(const cx<R> M[4], cx<R> c0, cx<R> c1, cx<R>& o0, cx<R>& o1) {
+  o0 = M[0] * c0 + M[1] * c1;
+  o1 = M[2] * c0 + M[3] * c1;
+}
+
+// Fbar Jslash F
+template <typename R>
+__device__ __forceinline__ cx<R> ffv_amp(const Sp<R>& a, const V4<R>& J, const Sp<R>& b) {
+  cx<R> X[4], Y[4];
+  sigma_blocks(J, X, Y);
+  cx<R> t0, t1, u0, u1;
+  mulcol(X, b.c[2], b.c[3], t0, t1);
+  mulcol(Y, b.c[0], b.c[1], u0, u1);
+  return a.c[0] * t0 + a.c[1] * t1 + a.c[2] * u0 + a.c[3] * u1;
+}
+
+// row current: coef * Fbar Jslash (Qslash + m)
+template <typename R>
+__device__ __forceinline__ Sp<R> ffv_row(const Sp<R>& a, const V4<R>& J, const R Q[4], R m, cx<R> coef) {
+  cx<R> X[4], Y[4], XQ[4], YQ[4];
+  sigma_blocks(J, X, Y);
+  sigma_blocks(Q, XQ, YQ);
+  cx<R> rL0, rL1, rR0, rR1;
+  rowmul(a.c[2], a.c[3], Y, rL0, rL1);  // (a_R Y, a_L X)
+  rowmul(a.c[0], a.c[1], X, rR0, rR1);
+  cx<R> s0, s1, t0, t1;
+  rowmul(rR0, rR1, YQ, s0, s1);  // m rL + rR YQ
+  rowmul(rL0, rL1, XQ, t0, t1);  // rL XQ + m rR
+  Sp<R> o;
+  o.c[0] = coef * fma(m, rL0, s0);
+  o.c[1] = coef * fma(m, rL1, s1);
+  o.c[2] = coef * fma(m, rR0, t0);
+  o.c[3] = coef * fma(m, rR1, t1);
+  return o;
+}
+
+// column current: coef * (qslash + m) Jslash F
+template <typename R>
+__device__ __forceinline__ Sp<R> ffv_col(const V4<R>& J, const Sp<R>& b, const R q[4], R m, cx<R> coef) {
+  cx<R> X[4], Y[4], XQ[4], YQ[4];
+  sigma_blocks(J, X, Y);
+  sigma_blocks(q, XQ, YQ);
+  cx<R> cL0, cL1, cR0, cR1;
+  mulcol(X, b.c[2], b.c[3], cL0, cL1);  // Jslash F = (X F_R, Y F_L)
+  mulcol(Y, b.c[0], b.c[1], cR0, cR1);
+  cx<R> s0, s1, t0, t1;
+  mulcol(XQ, cR0, cR1, s0, s1);  // m cL + XQ cR
+  mulcol(YQ, cL0, cL1, t0, t1);  // YQ cL + m cR
+  Sp<R> o;
+  o.c[0] = coef * fma(m, cL0, s0);
+  o.c[1] = coef * fma(m, cL1, s1);
+  o.c[2] = coef * fma(m, cR0, t0);
+  o.c[3] = coef * fma(m, cR1, t1);
+  return o;
+}
+
+// vector current coef * Fbar gamma^mu (cL PL + cR PR) F
+template <typename R>
+__device__ __forceinline__ V4<R> ffv_vcur(const Sp<R>& a, const Sp<R>& b, cx<R> coef, R cL = R(1), R cR = R(1)) {
+  // upper: (a0,a1) sigma^mu (b2,b3) [right-handed F], lower: (a2,a3) sigmabar^mu (b0,b1)
+  const cx<R> u02 = a.c[0] * b.c[2], u13 = a.c[1] * b.c[3], u03 = a.c[0] * b.c[3], u12 = a.c[1] * b.c[2];
+  const cx<R> l20 = a.c[2] * b.c[0], l31 = a.c[3] * b.c[1], l21 = a.c[2] * b.c[1], l30 = a.c[3] * b.c[0];
+  V4<R> g;
+  g.c[0] = cR * (u02 + u13) + cL * (l20 + l31);
+  g.c[1] = cR * (u03 + u12) - cL * (l21 + l30);
+  g.c[2] = cR * mul_i(u12 - u03) + cL * mul_i(l21 - l30);
+  g.c[3] = cR * (u02 - u13) - cL * (l20 - l31);
+  for (int mu = 0; mu < 4; mu++) g.c[mu] = coef * g.c[mu];
+  return g;
+}
+
+// three-gluon current: c * V3(kx, Jx, ky, Jy),
+//   V3 = (Jx.Jy)(kx-ky) + Jy (2ky+kx).Jx - Jx (2kx+ky).Jy
+template <typename R>
+__device__ __forceinline__ V4<R> vvv_cur(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy, R c) {
+  R a[4], b[4];
+  for (int mu = 0; mu < 4; mu++) {
+    a[mu] = R(2) * ky[mu] + kx[mu];
+    b[mu] = R(2) * kx[mu] + ky[mu];
+  }
+  const cx<R> xy = dot(Jx, Jy);
+  const cx<R> ax = dot(a, Jx);
+  const cx<R> by = dot(b, Jy);
+  V4<R> o;
+  for (int mu = 0; mu < 4; mu++) {
+    cx<R> t = (kx[mu] - ky[mu]) * xy;
+    t = t + Jy.c[mu] * ax;
+    t = t - Jx.c[mu] * by;
+    o.c[mu] = c * t;
+  }
+  return o;
+}
+// amplitude: c * V3(kx, Jx, ky, Jy) . G
+template <typename R>
+__device__ __forceinline__ cx<R> vvv_amp(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy,
+                                         const V4<R>& G, R c) {
+  R a[4], b[4], d[4];
+  for (int mu = 0; mu < 4; mu++) {
+    a[mu] = R(2) * ky[mu] + kx[mu];
+    b[mu] = R(2) * kx[mu] + ky[mu];
+    d[mu] = kx[mu] - ky[mu];
+  }
+  const cx<R> xy = dot(Jx, Jy);
+  const cx<R> t = xy * dot(d, G) + dot(Jy, G) * dot(a, Jx) - dot(Jx, G) * dot(b, Jy);
+  return c * t;
+}
+
+// four-gluon Lorentz structures for the three colour branches
+//   br 0: (X.Z) Y - (Y.Z) X     br 1: (X.Y) Z - (Y.Z) X     br 2: (X.Y) Z - (X.Z) Y
+template <int BR, typename R>
+__device__ __forceinline__ V4<R> vvvv_cur(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, R c) {
+  V4<R> o;
+  if (BR == 0) {
+    const cx<R> xz = dot(X, Z), yz = dot(Y, Z);
+    for (int mu = 0; mu < 4; mu++) o.c[mu] = c * (xz * Y.c[mu] - yz * X.c[mu]);
+  } else if (BR == 1) {
+    const cx<R> xy = dot(X, Y), yz = dot(Y, Z);
+    for (int mu = 0; mu < 4; mu++) o.c[mu] = c * (xy * Z.c[mu] - yz * X.c[mu]);
+  } else {
+    const cx<R> xy = dot(X, Y), xz = dot(X, Z);
+    for (int mu = 0; mu < 4; mu++) o.c[mu] = c * (xy * Z.c[mu] - xz * Y.c[mu]);
+  }
+  return o;
+}
+template <int BR, typename R>
+__device__ __forceinline__ cx<R> vvvv_amp(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, const V4<R>& G, R c) {
+  cx<R> t;
+  if (BR == 0) t = dot(X, Z) * dot(Y, G) - dot(Y, Z) * dot(X, G);
+  else if (BR == 1) t = dot(X, Y) * dot(Z, G) - dot(Y, Z) * dot(X, G);
+  else t = dot(X, Y) * dot(Z, G) - dot(X, Z) * dot(Y, G);
+  return c * t;
+}
+
+}  // namespace mg

@@ -1,0 +1,422 @@
+"""Emit straight-line CUDA for one process.
+
+For every process the generated header defines, as struct mg::<tag>:
+
+  constants   NPAR, NHEL, NCOL, NDIAG, NAMP, NSLOT, IDEN, CDEN, KNUM[NCOL*NCOL]
+  prepare<R>(p, kp, ev, es)          per event, FP64 arithmetic, results stored
+                                     as R in the per-thread slab ev[k*es]:
+                                     external-state ingredients, propagator
+                                     coefficients (-g/P^2, -g/(P^2-m^2+i m G))
+  amplitudes<R>(ev, es, hel, kp, jamp)  per helicity: external wavefunctions,
+                                     off-shell currents and amplitudes diagram
+                                     by diagram, accumulated into the colour
+                                     flows jamp[NCOL]
+  colour_quadratic<R>(jamp)          sum_ij KNUM_ij Re/Im(J_i) Re/Im(J_j)
+                                     (C = KNUM / CDEN)
+
+Helicity index convention: particle i has helicity +1 when bit (NPAR-1-i) of
+the index is set, -1 otherwise (index 0 = all negative).
+"""
+from __future__ import annotations
+
+from .colour import colour_matrix_exact, common_denominator, words
+from .diagrams import build_plan, count_diagrams
+
+PROCESSES = {
+    "e+ e- > mu+ mu-": ("eemumu", 0),
+    "g g > t t~": ("ggtt", 2),
+    "g g > t t~ g": ("ggttg", 3),
+    "g g > t t~ g g": ("ggttgg", 4),
+    "g g > t t~ g g g": ("ggttggg", 5),
+}
+
+
+def _fmt_knum(K) -> str:
+    return ", ".join(str(x) for row in K for x in row)
+
+
+class _Slots:
+    def __init__(self):
+        self.n = 0
+        self.names = {}
+
+    def alloc(self, name, size):
+        self.names[name] = self.n
+        self.n += size
+        return self.names[name]
+
+
+def _colour_quadratic(K, ncol) -> list[str]:
+    """Straight-line sum_ij K_ij (re_i re_j + im_i im_j) using symmetry."""
+    out = ["  R acc = R(0);"]
+    for i in range(ncol):
+        terms_r = []
+        terms_i = []
+        for j in range(i, ncol):
+            k = K[i][j] if j == i else 2 * K[i][j]
+            if k == 0:
+                continue
+            terms_r.append((k, f"jamp[{j}].re"))
+            terms_i.append((k, f"jamp[{j}].im"))
+        if not terms_r:
+            continue
+        k0, v0 = terms_r[0]
+        out.append(f"  {{ R yr = R({k0}) * {v0}; R yi = R({k0}) * {terms_i[0][1]};")
+        for (k, vr), (_, vi) in zip(terms_r[1:], terms_i[1:]):
+            out.append(f"    yr = fmaf_t<R>(R({k}), {vr}, yr); yi = fmaf_t<R>(R({k}), {vi}, yi);")
+        out.append(f"    acc = fmaf_t<R>(jamp[{i}].re, yr, acc); acc = fmaf_t<R>(jamp[{i}].im, yi, acc); }}")
+    out.append("  return acc;")
+    return out
+
+
+def emit_gg(n: int, tag: str) -> str:
+    npar = n + 2
+    nhel = 1 << npar
+    plan = build_plan(n)
+    ncol = len(plan.words)
+    C = colour_matrix_exact(n)
+    cden, K = common_denominator(C)
+    ndiag = count_diagrams(n)
+    iden = 4 * 64
+    for i in range(2, n - 1):
+        iden *= i
+    slots = [0, 1] + list(range(4, n + 2))  # gluon index -> particle slot
+    full = (1 << n) - 1
+
+    S = _Slots()
+    for i in range(n):
+        S.alloc(f"k{i}", 4)
+        S.alloc(f"e{i}", 6)
+    S.alloc("pt", 4)
+    S.alloc("ft", 5)
+    S.alloc("ptb", 4)
+    S.alloc("ftb", 5)
+    gmasks = sorted({op[-1] for op in plan.ops if op[0] in ("3", "4")})
+    fmasks = set()
+    for op in plan.ops:
+        if op[0] == "row":
+            fmasks.add(op[3])
+        elif op[0] == "col":
+            fmasks.add(full ^ op[3])
+    fmasks = sorted(fmasks)
+    for m in gmasks:
+        S.alloc(f"cg{m}", 1)
+    for m in fmasks:
+        S.alloc(f"cf{m}", 2)
+    S.alloc("cgtt", 1)
+    nslot = S.n
+    sl = S.names
+
+    L = []
+    L.append(f"// generated by paper_2303_18244_gb300.generator for 'g g > t t~{' g' * (n - 2)}'")
+    L.append("#pragma once")
+    L.append('#include "mg_vertices.cuh"')
+    L.append("namespace mg {")
+    L.append(f"struct {tag} {{")
+    L.append(f"static constexpr int NPAR = {npar};")
+    L.append(f"static constexpr int NHEL = {nhel};")
+    L.append(f"static constexpr int NCOL = {ncol};")
+    L.append(f"static constexpr int NDIAG = {ndiag};")
+    L.append(f"static constexpr int NAMP = {len(plan.amps)};")
+    L.append(f"static constexpr int NSLOT = {nslot};")
+    L.append(f"static constexpr double IDEN = {iden}.0;")
+    L.append(f"static constexpr int CDEN = {cden};")
+    L.append(f"static constexpr int KNUM[NCOL * NCOL] = {{{_fmt_knum(K)}}};")
+    L.append("")
+    # ---------------- prepare ----------------
+    L.append("// per-event ingredients (FP64 arithmetic), stored as R in ev[k * es]")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void prepare(const double* __restrict__ p, const double* __restrict__ kp,")
+    L.append("                                        R* __restrict__ ev, const int es) {")
+    L.append("  const double g = kp[0], mt = kp[1], wt = kp[2];")
+    L.append("#define EV(k) ev[(k) * es]")
+    for i in range(n):
+        s = slots[i]
+        sign = "" if s < 2 else "-"
+        L.append(f"  double k{i}[4] = {{{', '.join(f'{sign}p[{4 * s + mu}]' for mu in range(4))}}};")
+        L.append(f"  {{ double b[6]; vector_basis(p + {4 * s}, b);")
+        for mu in range(4):
+            L.append(f"    EV({sl[f'k{i}'] + mu}) = R(k{i}[{mu}]);")
+        for j in range(6):
+            L.append(f"    EV({sl[f'e{i}'] + j}) = R(b[{j}]);")
+        L.append("  }")
+    for name, s in (("pt", 2), ("ptb", 3)):
+        fname = "ft" if name == "pt" else "ftb"
+        L.append(f"  {{ double f[5]; fermion_ingredients(p + {4 * s}, mt, f);")
+        for mu in range(4):
+            L.append(f"    EV({sl[name] + mu}) = R(p[{4 * s + mu}]);")
+        for j in range(5):
+            L.append(f"    EV({sl[fname] + j}) = R(f[{j}]);")
+        L.append("  }")
+
+    def ksum_fp64(mask):
+        idx = [i for i in range(n) if mask >> i & 1]
+        return [" + ".join(f"k{i}[{mu}]" for i in idx) for mu in range(4)]
+
+    for m in gmasks:
+        comps = ksum_fp64(m)
+        L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
+        L.append("    const double P2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];")
+        L.append(f"    EV({sl[f'cg{m}']}) = R(-g / P2); }}")
+    for m in fmasks:
+        comps = ksum_fp64(m) if m else ["0.0"] * 4
+        L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
+        L.append("    double Q[4]; for (int mu = 0; mu < 4; mu++) Q[mu] = p[8 + mu] - K[mu];")
+        L.append("    const double dre = Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3] - mt * mt;")
+        L.append("    const double dim = mt * wt;")
+        L.append("    const double r = -g / (dre * dre + dim * dim);")
+        L.append(f"    EV({sl[f'cf{m}']}) = R(r * dre); EV({sl[f'cf{m}'] + 1}) = R(-r * dim); }}")
+    comps = ksum_fp64(full)
+    L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
+    L.append("    const double P2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];")
+    L.append(f"    EV({sl['cgtt']}) = R(g / P2); }}")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("")
+    # ---------------- amplitudes ----------------
+    L.append("// one helicity: currents and amplitudes, diagram by diagram, into the colour flows")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
+    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("  const R g = R(kp[0]);")
+    L.append("  const R mt = R(kp[1]);")
+    for i in range(npar):
+        L.append(f"  const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
+    L.append(f"  for (int c = 0; c < {ncol}; c++) jamp[c] = {{R(0), R(0)}};")
+    # momenta (R) on demand
+    emitted_k = set()
+
+    def kname(mask):
+        if mask in emitted_k:
+            return f"K{mask}"
+        idx = [i for i in range(n) if mask >> i & 1]
+        comps = []
+        for mu in range(4):
+            comps.append(" + ".join(f"EV({sl[f'k{i}'] + mu})" for i in idx))
+        L.append(f"  const R K{mask}[4] = {{{', '.join(comps)}}};")
+        emitted_k.add(mask)
+        return f"K{mask}"
+
+    emitted = {}
+
+    def cur(cid):
+        """Emit current cid (and its dependencies) if not yet emitted; return its name."""
+        if cid in emitted:
+            return emitted[cid]
+        op = plan.ops[cid]
+        kind = op[0]
+        name = f"w{cid}"
+        if kind == "ext":
+            i = op[1]
+            s = slots[i]
+            e = sl[f"e{i}"]
+            out = "true" if s >= 2 else "false"
+            L.append(f"  V4<R> {name};")
+            L.append(f"  {{ const R e1[3] = {{EV({e}), EV({e + 1}), EV({e + 2})}}; "
+                     f"const R e2[3] = {{EV({e + 3}), EV({e + 4}), EV({e + 5})}};")
+            L.append(f"    {name} = ext_vector<R>(e1, e2, R(l{s}), {out}); }}")
+        elif kind == "ubar":
+            f = sl["ft"]
+            L.append(f"  const Sp<R> {name} = ext_ubar<R>(FermIngr<R>{{EV({f}), EV({f + 1}), EV({f + 2}), "
+                     f"EV({f + 3}), EV({f + 4})}}, l2);")
+        elif kind == "v":
+            f = sl["ftb"]
+            L.append(f"  const Sp<R> {name} = ext_v<R>(FermIngr<R>{{EV({f}), EV({f + 1}), EV({f + 2}), "
+                     f"EV({f + 3}), EV({f + 4})}}, l3);")
+        elif kind == "gtt":
+            a = cur(plan.keys[("row", ())])
+            b = cur(plan.keys[("col", ())])
+            L.append(f"  const V4<R> {name} = ffv_vcur<R>({a}, {b}, cx<R>{{R(0), EV({sl['cgtt']})}});")
+        elif kind == "3":
+            x, y, m = op[1], op[2], op[3]
+            nx, ny = cur(x), cur(y)
+            kx, ky = kname(_mask_of(plan, x)), kname(_mask_of(plan, y))
+            L.append(f"  const V4<R> {name} = vvv_cur<R>({kx}, {nx}, {ky}, {ny}, EV({sl[f'cg{m}']}));")
+        elif kind == "4":
+            x, y, z, br, m = op[1:]
+            nx, ny, nz = cur(x), cur(y), cur(z)
+            sign = "-" if br in (0, 1) else ""
+            L.append(f"  const V4<R> {name} = vvvv_cur<{br}, R>({nx}, {ny}, {nz}, {sign}g * EV({sl[f'cg{m}']}));")
+        elif kind == "row":
+            prev, gid, m = op[1], op[2], op[3]
+            npv, ng = cur(prev), cur(gid)
+            c = sl[f"cf{m}"]
+            km = kname(m)
+            L.append(f"  Sp<R> {name};")
+            L.append(f"  {{ const R Q[4] = {{EV({sl['pt']}) - {km}[0], EV({sl['pt'] + 1}) - {km}[1], "
+                     f"EV({sl['pt'] + 2}) - {km}[2], EV({sl['pt'] + 3}) - {km}[3]}};")
+            L.append(f"    {name} = ffv_row<R>({npv}, {ng}, Q, mt, cx<R>{{EV({c}), EV({c + 1})}}); }}")
+        elif kind == "col":
+            gid, nxt, m = op[1], op[2], op[3]
+            ng, nn = cur(gid), cur(nxt)
+            c = sl[f"cf{full ^ m}"]
+            km = kname(m)
+            L.append(f"  Sp<R> {name};")
+            L.append(f"  {{ const R q[4] = {{{km}[0] - EV({sl['ptb']}), {km}[1] - EV({sl['ptb'] + 1}), "
+                     f"{km}[2] - EV({sl['ptb'] + 2}), {km}[3] - EV({sl['ptb'] + 3})}};")
+            L.append(f"    {name} = ffv_col<R>({ng}, {nn}, q, mt, cx<R>{{EV({c}), EV({c + 1})}}); }}")
+        else:
+            raise ValueError(kind)
+        emitted[cid] = name
+        return name
+
+    # order amplitudes so that those sharing late currents are adjacent
+    def deps(op):
+        return op[1:4] if op[0] != "a4" else op[1:4]
+
+    order = sorted(range(len(plan.amps)), key=lambda i: (max(deps(plan.amps[i][0])), i))
+    gtt_id = plan.keys.get(("gtt",))
+    for ai in order:
+        op, co = plan.amps[ai]
+        if op[0] == "f":
+            r, gq, c = cur(op[1]), cur(op[2]), cur(op[3])
+            expr = f"mul_i(g * ffv_amp<R>({r}, {gq}, {c}))"
+        elif op[0] == "a3":
+            G = cur(gtt_id)
+            nx, ny = cur(op[1]), cur(op[2])
+            kx, ky = kname(_mask_of(plan, op[1])), kname(_mask_of(plan, op[2]))
+            expr = f"vvv_amp<R>({kx}, {nx}, {ky}, {ny}, {G}, -g)"
+        else:
+            G = cur(gtt_id)
+            nx, ny, nz = cur(op[1]), cur(op[2]), cur(op[3])
+            br = op[4]
+            c = "g * g" if br in (0, 1) else "-g * g"
+            expr = f"vvvv_amp<{br}, R>({nx}, {ny}, {nz}, {G}, {c})"
+        L.append(f"  {{ const cx<R> a = {expr};")
+        parts = []
+        for k, c in sorted(co.items()):
+            if c == 1:
+                parts.append(f"jamp[{k}] = jamp[{k}] + a;")
+            elif c == -1:
+                parts.append(f"jamp[{k}] = jamp[{k}] - a;")
+            else:
+                parts.append(f"jamp[{k}] = fma(R({c}), a, jamp[{k}]);")
+        L.append("    " + " ".join(parts) + " }")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("")
+    L.append("// sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j); |M|^2 colour sum = result / CDEN")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp) {")
+    L.extend(_colour_quadratic(K, ncol))
+    L.append("}")
+    L.append(f"}};  // struct {tag}")
+    L.append("}  // namespace mg")
+    return "\n".join(L) + "\n"
+
+
+def _mask_of(plan, cid) -> int:
+    op = plan.ops[cid]
+    if op[0] == "ext":
+        return 1 << op[1]
+    if op[0] == "3":
+        return op[3]
+    if op[0] == "4":
+        return op[5]
+    raise ValueError(op)
+
+
+def emit_eemumu(tag: str) -> str:
+    """e+(0) e-(1) -> mu+(2) mu-(3): s-channel photon and Z (2 diagrams).
+    kp = {e^2, gz^2, gL, gR, MZ, WZ}; amp = e^2/s Je.Jm + gz^2/(s - MZ^2 + i MZ WZ) JZe.JZm."""
+    L = []
+    L.append("// generated by paper_2303_18244_gb300.generator for 'e+ e- > mu+ mu-'")
+    L.append("#pragma once")
+    L.append('#include "mg_vertices.cuh"')
+    L.append("namespace mg {")
+    L.append(f"struct {tag} {{")
+    L.append("static constexpr int NPAR = 4;")
+    L.append("static constexpr int NHEL = 16;")
+    L.append("static constexpr int NCOL = 1;")
+    L.append("static constexpr int NDIAG = 2;")
+    L.append("static constexpr int NAMP = 2;")
+    L.append("static constexpr int NSLOT = 23;")
+    L.append("static constexpr double IDEN = 4.0;")
+    L.append("static constexpr int CDEN = 1;")
+    L.append("static constexpr int KNUM[1] = {1};")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void prepare(const double* __restrict__ p, const double* __restrict__ kp,")
+    L.append("                                        R* __restrict__ ev, const int es) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("  for (int i = 0; i < 4; i++) {")
+    L.append("    double f[5]; fermion_ingredients(p + 4 * i, 0.0, f);")
+    L.append("    for (int j = 0; j < 5; j++) EV(5 * i + j) = R(f[j]);")
+    L.append("  }")
+    L.append("  const double P[4] = {p[0] + p[4], p[1] + p[5], p[2] + p[6], p[3] + p[7]};")
+    L.append("  const double s = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];")
+    L.append("  EV(20) = R(kp[0] / s);")
+    L.append("  const double dre = s - kp[4] * kp[4], dim = kp[4] * kp[5];")
+    L.append("  const double r = kp[1] / (dre * dre + dim * dim);")
+    L.append("  EV(21) = R(r * dre); EV(22) = R(-r * dim);")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
+    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("#define ING(i) FermIngr<R>{EV(5 * (i)), EV(5 * (i) + 1), EV(5 * (i) + 2), EV(5 * (i) + 3), EV(5 * (i) + 4)}")
+    for i in range(4):
+        L.append(f"  const int l{i} = ((hel >> {3 - i}) & 1) ? 1 : -1;")
+    L.append("  const Sp<R> w0 = ext_vbar<R>(ING(0), l0);")
+    L.append("  const Sp<R> w1 = ext_u<R>(ING(1), l1);")
+    L.append("  const Sp<R> w2 = ext_v<R>(ING(2), l2);")
+    L.append("  const Sp<R> w3 = ext_ubar<R>(ING(3), l3);")
+    L.append("  const cx<R> one = {R(1), R(0)};")
+    L.append("  const R gl = R(kp[2]), gr = R(kp[3]);")
+    L.append("  const V4<R> ja = ffv_vcur<R>(w0, w1, one);")
+    L.append("  const V4<R> la = ffv_vcur<R>(w3, w2, one);")
+    L.append("  const V4<R> jz = ffv_vcur<R>(w0, w1, one, gl, gr);")
+    L.append("  const V4<R> lz = ffv_vcur<R>(w3, w2, one, gl, gr);")
+    L.append("  const cx<R> amp_a = EV(20) * dot(ja, la);")
+    L.append("  const cx<R> amp_z = cx<R>{EV(21), EV(22)} * dot(jz, lz);")
+    L.append("  jamp[0] = amp_a + amp_z;")
+    L.append("#undef ING")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp) {")
+    L.append("  return jamp[0].re * jamp[0].re + jamp[0].im * jamp[0].im;")
+    L.append("}")
+    L.append(f"}};  // struct {tag}")
+    L.append("}  // namespace mg")
+    return "\n".join(L) + "\n"
+
+
+def emit(proc: str) -> tuple[str, str]:
+    """(tag, header source) for a process string."""
+    tag, n = PROCESSES[proc]
+    if n == 0:
+        return tag, emit_eemumu(tag)
+    return tag, emit_gg(n, tag)
+
+
+# threads per CTA: FP64 path / mixed path (shared-memory slab sizes differ)
+THREADS = {
+    "eemumu": (128, 128),
+    "ggtt": (128, 128),
+    "ggttg": (128, 128),
+    "ggttgg": (64, 128),
+    "ggttggg": (64, 128),
+}
+
+
+def emit_kernels_tu(proc: str) -> tuple[str, str]:
+    """Translation unit instantiating the kernels of one process."""
+    tag, _ = PROCESSES[proc]
+    nt64, nt32 = THREADS[tag]
+    src = f"""// generated by paper_2303_18244_gb300.generator: kernels of '{proc}'
+#include "../mg_kernels.cuh"
+#include "{tag}.cuh"
+
+namespace mg {{
+static int sigma_fp64(const LaunchArgs& a) {{ return launch_sigma<{tag}, double, {nt64}>(a); }}
+static int sigma_mixed(const LaunchArgs& a) {{ return launch_sigma<{tag}, float, {nt32}>(a); }}
+static int helicities(const LaunchArgs& a) {{ return launch_helicities<{tag}, {nt64}>(a); }}
+static const ProcDesc desc = {{"{proc}", "{tag}", {tag}::NPAR, {tag}::NHEL, {tag}::NCOL, {tag}::NDIAG,
+                              {tag}::NAMP, {tag}::IDEN, {tag}::CDEN, {tag}::KNUM,
+                              sigma_fp64, sigma_mixed, helicities}};
+const ProcDesc* proc_{tag}() {{ return &desc; }}
+}}  // namespace mg
+"""
+    return tag, src

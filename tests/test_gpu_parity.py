@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 path: relative error <= 1e-12 per event (the FP64 bar of the workload).
+Mixed path: median relative error <= 1e-5, with p99 and max bounded.
+Small cases span several CTAs plus a ragged tail; the full workload sizes are
+checked on sampled events in the launch configuration bench.py times.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2303_18244_gb300 import mg  # noqa: E402
+from paper_2303_18244_gb300.inputs import process_momenta  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# process -> (sqrt(s), seed, small-case size, full workload size)
+WORKLOADS = {
+    "e+ e- > mu+ mu-": (500.0, 1, 1000, 16384),
+    "g g > t t~": (1000.0, 2, 1000, 524288),
+    "g g > t t~ g": (1200.0, 6, 300, 65536),
+    "g g > t t~ g g": (1500.0, 3, 300, 524288),
+    "g g > t t~ g g g": (2000.0, 4, 130, 65536),
+}
+PROCS = list(WORKLOADS)
+TAGS = {"e+ e- > mu+ mu-": "eemumu", "g g > t t~": "ggtt", "g g > t t~ g": "ggttg",
+        "g g > t t~ g g": "ggttgg", "g g > t t~ g g g": "ggttggg"}
+
+
+def _ids(p):
+    return TAGS.get(p, str(p))
+
+
+def _have(proc):
+    try:
+        mg.Process(proc).close()
+        return True
+    except mg.MGError as e:
+        if e.code == -1:
+            return False
+        raise
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gpu_me(h, p, stream=None):
+    mom = _dev(p)
+    out = torch.full((p.shape[0],), float("nan"), dtype=torch.float64, device="cuda")
+    if stream is not None:
+        stream.wait_stream(torch.cuda.current_stream())
+    mg.sigma(h, mom, out, stream=stream)
+    torch.cuda.synchronize()
+    assert mg.process_status(h) == 0
+    return out.cpu().numpy()
+
+
+def _rel(x, y):
+    return np.abs(x - y) / np.abs(y)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("proc", PROCS, ids=_ids)
+def test_fp64_parity_small(proc):
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, n, _ = WORKLOADS[proc]
+    p = process_momenta(proc, rs, n, seed)
+    h = mg.Process(proc)
+    got = _gpu_me(h, p)
+    ref = O.me(proc, p)
+    r = _rel(got, ref)
+    assert np.all(np.isfinite(got))
+    assert r.max() <= 1e-12, f"max rel err {r.max():.3e} at event {int(r.argmax())}"
+
+
+@pytest.mark.parametrize("proc", PROCS, ids=_ids)
+def test_mixed_parity_small(proc):
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, n, _ = WORKLOADS[proc]
+    p = process_momenta(proc, rs, n, seed)
+    h = mg.Process(proc, precision=mg.MG_MIXED)
+    got = _gpu_me(h, p)
+    ref = O.me(proc, p)
+    r = _rel(got, ref)
+    print(f"{proc}: mixed rel err median {np.median(r):.2e} p99 {np.quantile(r, 0.99):.2e} max {r.max():.2e}")
+    assert np.median(r) <= 1e-5
+    assert np.quantile(r, 0.99) <= 1e-3
+    assert r.max() <= 1e-2
+
+
+@pytest.mark.parametrize("proc", PROCS, ids=_ids)
+@pytest.mark.parametrize("precision", [mg.MG_FP64, mg.MG_MIXED], ids=["fp64", "mixed"])
+def test_full_size_sampled(proc, precision):
+    """Full workload size, bench launch configuration, sampled events vs oracle."""
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, _, nfull = WORKLOADS[proc]
+    p = process_momenta(proc, rs, nfull, seed)
+    h = mg.Process(proc, precision=precision)
+    calib = process_momenta(proc, rs, 1024, seed + 1000)
+    mg.good_helicities(h, _dev(calib))
+    got = _gpu_me(h, p)
+    assert np.all(np.isfinite(got)) and np.all(got > 0)
+    rng = np.random.default_rng(seed)
+    nsamp = 24 if proc == "g g > t t~ g g g" else 64
+    idx = np.unique(np.concatenate([[0, 127, 128, nfull - 1], rng.integers(0, nfull, nsamp)]))
+    ref = O.me(proc, p[idx])
+    r = _rel(got[idx], ref)
+    if precision == mg.MG_FP64:
+        assert r.max() <= 1e-12, f"max rel err {r.max():.3e}"
+    else:
+        assert np.median(r) <= 1e-5 and r.max() <= 1e-2
+
+
+def test_good_helicities_eemumu():
+    """Massless e+e- -> mu+mu-: exactly the 4 chirality-conserving combinations survive."""
+    proc = "e+ e- > mu+ mu-"
+    h = mg.Process(proc)
+    calib = process_momenta(proc, 500.0, 1024, 1001)
+    n, mask = mg.good_helicities(h, _dev(calib))
+    assert n == 4
+    # helicity index bits: particle i <-> bit (3 - i), 1 = +; e+ e- mu+ mu-
+    good = {i for i in range(16) if mask[i]}
+    want = set()
+    for i in range(16):
+        l = [1 if (i >> (3 - k)) & 1 else -1 for k in range(4)]
+        if l[0] == -l[1] and l[2] == -l[3]:
+            want.add(i)
+    assert good == want
+
+
+@pytest.mark.parametrize("proc", PROCS, ids=_ids)
+def test_good_helicities_masked_sum_equals_full(proc):
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, n, _ = WORKLOADS[proc]
+    h = mg.Process(proc)
+    fresh = process_momenta(proc, rs, min(n, 256), seed + 7)
+    full = _gpu_me(h, fresh)
+    calib = process_momenta(proc, rs, 1024, seed + 1000)
+    ngood, mask = mg.good_helicities(h, _dev(calib))
+    assert 1 <= ngood <= h.info.n_hel and mask.sum() == ngood
+    masked = _gpu_me(h, fresh)
+    assert np.max(_rel(masked, full)) <= 1e-14 * 10
+    # per-helicity values sum to the ME
+    out = torch.empty((fresh.shape[0], h.info.n_hel), dtype=torch.float64, device="cuda")
+    mg.sigma_helicities(h, _dev(fresh), out)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.sum(1).cpu().numpy(), full, rtol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 127, 128, 129, 257])
+def test_ragged_sizes(n):
+    proc = "g g > t t~ g"
+    p = process_momenta(proc, 1200.0, n, 17)
+    h = mg.Process(proc)
+    got = _gpu_me(h, p)
+    np.testing.assert_allclose(got, O.me(proc, p), rtol=1e-12)
+
+
+def test_zero_events_and_bad_arguments():
+    h = mg.Process("g g > t t~")
+    mom = torch.zeros((0, 4, 4), dtype=torch.float64, device="cuda")
+    out = torch.zeros((0,), dtype=torch.float64, device="cuda")
+    assert mg.lib().mg_sigma(h.handle, None, 0, None, None) == 0
+    mg.sigma(h, mom, out)
+    p = _dev(process_momenta("g g > t t~", 1000.0, 8, 2))
+    o = torch.empty(8, dtype=torch.float64, device="cuda")
+    assert mg.lib().mg_sigma(h.handle, p.data_ptr(), -1, o.data_ptr(), None) == -2
+    assert mg.lib().mg_sigma(h.handle, p.data_ptr() + 8, 4, o.data_ptr(), None) == -2  # misaligned
+    assert mg.lib().mg_sigma(None, p.data_ptr(), 8, o.data_ptr(), None) == -2
+    with pytest.raises(mg.MGError) as ei:
+        mg.Process("u u~ > t t~")
+    assert ei.value.code == -1
+    with pytest.raises(mg.MGError):
+        mg.Process("g g > t t~", precision=7)
+
+
+def test_sigma_host_matches_device_and_stream():
+    proc = "g g > t t~ g g"
+    p = process_momenta(proc, 1500.0, 300, 23)
+    h = mg.Process(proc, precision=mg.MG_MIXED)
+    s = torch.cuda.Stream()
+    dev = _gpu_me(h, p, stream=s)
+    out = np.empty(p.shape[0])
+    mg.sigma_host(h, p, out)
+    np.testing.assert_array_equal(out, dev)
+
+
+def test_no_top_width_flag_matches_oracle():
+    proc = "g g > t t~ g"
+    p = process_momenta(proc, 1200.0, 200, 29)
+    h = mg.Process(proc, flags=mg.MG_NO_TOP_WIDTH)
+    np.testing.assert_allclose(_gpu_me(h, p), O.me(proc, p, O.Params(wt=0.0)), rtol=1e-12)
+
+
+def test_photon_only_closed_form():
+    proc = "e+ e- > mu+ mu-"
+    p = process_momenta(proc, 500.0, 1000, 1)
+    h = mg.Process(proc, flags=mg.MG_PHOTON_ONLY)
+    got = _gpu_me(h, p)
+    e2 = 4 * np.pi / 132.507
+    a, b = p[:, 1, 1:], p[:, 3, 1:]
+    c = (a * b).sum(-1) / np.linalg.norm(a, axis=1) / np.linalg.norm(b, axis=1)
+    np.testing.assert_allclose(got, e2 ** 2 * (1 + c ** 2), rtol=1e-12)
