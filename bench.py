@@ -186,9 +186,9 @@ def main():
 
     from paper_2303_18244_gb300 import mg
     from paper_2303_18244_gb300.inputs import process_momenta
+    from paper_2303_18244_gb300.shard import barrier, event_block, max_over_ranks
 
-    nevt = args.nevt
-    first = rank * nevt
+    first, nevt = event_block(rank, world, args.nevt)
     p = process_momenta(PROC, SQRTS, nevt, SEED, first_event=first)
     calib = process_momenta(PROC, SQRTS, 1024, SEED + 1000)
     mom = torch.from_numpy(p).cuda()
@@ -206,8 +206,7 @@ def main():
         for _ in range(warmup):
             mg.sigma(h, mom, o, stream)
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        barrier()
         torch.cuda.synchronize()
         per = []
         for _ in range(steps):
@@ -220,8 +219,7 @@ def main():
             per.append((e0, e1))
         torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in per]
-        if world > 1:
-            torch.distributed.barrier()
+        barrier()
         return ms
 
     clocks = ClockSampler(local)
@@ -232,12 +230,7 @@ def main():
     ms_64 = timed(h64, out64, args.fp64_steps, 1)
     assert mg.process_status(h64) == 0
 
-    t_mix = sum(ms_mix)
-    t_64 = sum(ms_64) / len(ms_64)
-    if world > 1:
-        t = torch.tensor([t_mix, t_64], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_mix, t_64 = t.tolist()
+    t_mix, t_64 = max_over_ranks([sum(ms_mix), sum(ms_64) / len(ms_64)], device="cuda")
     value = world * nevt * args.steps / (t_mix * 1e-3)
     value64 = world * nevt / (t_64 * 1e-3)
 
@@ -257,11 +250,7 @@ def main():
         t0 = time.perf_counter()
         mg.sigma_host(hmix, hp, ho, stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_t = statistics.median(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = t.item()
+    e2e_t = max_over_ranks([statistics.median(e2e_ms)], device="cuda")[0]
 
     fl = load_flops("ggttgg")
     flops_evt = ngood * (fl["amp_flops_per_hel"] + fl["colour_dense_flops_per_hel"])

@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mg_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIBDIR, "libmgoracle.so")
+_LIB_EXT = os.path.join(_LIBDIR, "libmgoracle_ext.so")
 
 PROCS = {
     "e+ e- > mu+ mu-": 0,
@@ -50,24 +51,52 @@ class Params:
 
 
 def build(force: bool = False) -> str:
-    """Compile mg_oracle.c into a shared library with gcc (plain C11)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
+    """Compile mg_oracle.c with gcc (plain C11): the FP64 oracle and its
+    extended-precision twin (same source, long double arithmetic)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-fcx-limited-range", "-ffp-contract=off",
-           "-o", tmp, _SRC, "-lm", "-lpthread"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    for lib_path, extra in ((_LIB, []), (_LIB_EXT, ["-DORACLE_REAL=long double"])):
+        if (not force and os.path.exists(lib_path)
+                and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC)):
+            continue
+        tmp = lib_path + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-fcx-limited-range", "-ffp-contract=off",
+               *extra, "-o", tmp, _SRC, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, lib_path)
     return _LIB
 
 
 _lib = None
+_lib_ext = None
 _lib_lock = threading.Lock()
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
+
+
+def _declare(L):
+    L.mgo_me.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int64, _D]
+    for name in ("mgo_ordered_amps", "mgo_ordered_colour_sum", "mgo_dressed_colour_sum"):
+        getattr(L, name).argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D]
+    L.mgo_colour_matrix.argtypes = [ctypes.c_int, _D]
+    L.mgo_permutations.argtypes = [ctypes.c_int, _I]
+    L.mgo_generators.argtypes = [_D]
+    L.mgo_fabc.argtypes = [_D]
+    L.mgo_spinor.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_int, _D]
+    L.mgo_polarisation.argtypes = [_D, ctypes.c_int, _D]
+    L.mgo_gamma.argtypes = [_D]
+    L.mgo_npar.argtypes = [ctypes.c_int]
+    return L
+
+
+def lib_ext():
+    """The extended-precision (long double) build of the same oracle source."""
+    global _lib_ext
+    with _lib_lock:
+        if _lib_ext is None:
+            build()
+            _lib_ext = _declare(ctypes.CDLL(_LIB_EXT))
+    return _lib_ext
 
 
 def lib():
@@ -100,15 +129,16 @@ def _check(rc: int):
 
 
 def me(proc: str, momenta: np.ndarray, params: Params | None = None,
-       threads: int | None = None) -> np.ndarray:
-    """Per-event ME (mg_oracle.c: mgo_me), events split over host threads."""
+       threads: int | None = None, extended: bool = False) -> np.ndarray:
+    """Per-event ME (mg_oracle.c: mgo_me), events split over host threads.
+    extended=True evaluates in long double (the adjudicator at the 1e-12 level)."""
     params = params or Params()
     pid = PROCS[proc]
     mom = np.ascontiguousarray(momenta, dtype=np.float64)
     nevt = mom.shape[0]
     out = np.empty(nevt, dtype=np.float64)
     pa = params.array()
-    L = lib()
+    L = lib_ext() if extended else lib()
     if proc != "e+ e- > mu+ mu-":
         colour_matrix(pid + 1)  # fill the colour-matrix cache once, outside the pool
     threads = threads or os.cpu_count() or 1

@@ -47,13 +47,21 @@
  * f^{abc} summed over every colour assignment.
  */
 #include <complex.h>
-#include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
 
-typedef double complex cplx;
+/* Arithmetic type: double by default; the same source built with
+ * -DORACLE_REAL="long double" gives the extended-precision variant used to
+ * adjudicate disagreements at the 1e-12 level. */
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+typedef ORACLE_REAL complex cplx;
+static const real PI_R = 3.14159265358979323846264338327950288L;
 
 #define MGO_OK 0
 #define MGO_ERR_ARG (-1)
@@ -65,7 +73,7 @@ enum { MGO_EEMUMU = 0, MGO_GGTT = 1, MGO_GGTTG = 2, MGO_GGTTGG = 3, MGO_GGTTGGG 
 #define MAXPERM 120
 
 typedef struct {
-  double mt, wt, alpha_s, mz, wz, alpha_em_inv, gf;
+  real mt, wt, alpha_s, mz, wz, alpha_em_inv, gf;
   int photon_only;
 } oparams;
 
@@ -124,19 +132,19 @@ __attribute__((constructor)) static void init_tables(void) {
   TGEN[4][0][2] = -0.5 * I; TGEN[4][2][0] = 0.5 * I;
   TGEN[5][1][2] = 0.5; TGEN[5][2][1] = 0.5;
   TGEN[6][1][2] = -0.5 * I; TGEN[6][2][1] = 0.5 * I;
-  const double r3 = 1.0 / (2.0 * sqrt(3.0));
+  const real r3 = 1 / (2 * sqrt((real)3));
   TGEN[7][0][0] = r3; TGEN[7][1][1] = r3; TGEN[7][2][2] = -2.0 * r3;
 }
 
-static const double METRIC[4] = {1.0, -1.0, -1.0, -1.0};
+static const real METRIC[4] = {1.0, -1.0, -1.0, -1.0};
 
 static cplx dot_cc(const cplx a[4], const cplx b[4]) {
   return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
-static cplx dot_rc(const double a[4], const cplx b[4]) {
+static cplx dot_rc(const real a[4], const cplx b[4]) {
   return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
-static double dot_rr(const double a[4], const double b[4]) {
+static real dot_rr(const real a[4], const real b[4]) {
   return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
 
@@ -149,7 +157,7 @@ static void slash_c(const cplx v[4], cplx S[4][4]) {
       S[r][c] = s;
     }
 }
-static void slash_r(const double v[4], cplx S[4][4]) {
+static void slash_r(const real v[4], cplx S[4][4]) {
   cplx vc[4] = {v[0], v[1], v[2], v[3]};
   slash_c(vc, S);
 }
@@ -181,8 +189,8 @@ static cplx rowcol(const cplx r[4], const cplx c[4]) {
 
 /* Dirac spinor u(p, s), spin-z basis chi_1 = (1,0), chi_2 = (0,1):
  *   u = [ sqrt(E+m) chi ; (sigma.p) chi / sqrt(E+m) ]                 */
-static void spinor_u(const double p[4], double m, int s, cplx u[4]) {
-  const double a = sqrt(p[0] + m);
+static void spinor_u(const real p[4], real m, int s, cplx u[4]) {
+  const real a = sqrt(p[0] + m);
   const cplx chi[2] = {s == 0 ? 1.0 : 0.0, s == 0 ? 0.0 : 1.0};
   /* sigma.p = [[pz, px - i py], [px + i py, -pz]] */
   const cplx sp0 = p[3] * chi[0] + (p[1] - I * p[2]) * chi[1];
@@ -193,8 +201,8 @@ static void spinor_u(const double p[4], double m, int s, cplx u[4]) {
   u[3] = sp1 / a;
 }
 /* v(p, s) = [ (sigma.p) eta / sqrt(E+m) ; sqrt(E+m) eta ] */
-static void spinor_v(const double p[4], double m, int s, cplx v[4]) {
-  const double a = sqrt(p[0] + m);
+static void spinor_v(const real p[4], real m, int s, cplx v[4]) {
+  const real a = sqrt(p[0] + m);
   const cplx eta[2] = {s == 0 ? 1.0 : 0.0, s == 0 ? 0.0 : 1.0};
   const cplx sp0 = p[3] * eta[0] + (p[1] - I * p[2]) * eta[1];
   const cplx sp1 = (p[1] + I * p[2]) * eta[0] - p[3] * eta[1];
@@ -214,18 +222,18 @@ static void dirac_bar(const cplx in[4], cplx out[4]) {
 /* Real linear polarisation vectors of a massless vector with momentum k:
  * eps^0 = 0, eps.k = 0, orthonormal.  e1 = unit(n x khat) with n the
  * coordinate axis least aligned with k, e2 = khat x e1.                 */
-static void polarisation(const double k[4], int which, double eps[4]) {
-  const double kk = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
-  const double kh[3] = {k[1] / kk, k[2] / kk, k[3] / kk};
+static void polarisation(const real k[4], int which, real eps[4]) {
+  const real kk = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+  const real kh[3] = {k[1] / kk, k[2] / kk, k[3] / kk};
   int ax = 0;
   for (int i = 1; i < 3; i++)
     if (fabs(kh[i]) < fabs(kh[ax])) ax = i;
-  double n[3] = {0, 0, 0};
+  real n[3] = {0, 0, 0};
   n[ax] = 1.0;
-  double e1[3] = {n[1] * kh[2] - n[2] * kh[1], n[2] * kh[0] - n[0] * kh[2], n[0] * kh[1] - n[1] * kh[0]};
-  const double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  real e1[3] = {n[1] * kh[2] - n[2] * kh[1], n[2] * kh[0] - n[0] * kh[2], n[0] * kh[1] - n[1] * kh[0]};
+  const real l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
   for (int i = 0; i < 3; i++) e1[i] /= l1;
-  const double e2[3] = {kh[1] * e1[2] - kh[2] * e1[1], kh[2] * e1[0] - kh[0] * e1[2], kh[0] * e1[1] - kh[1] * e1[0]};
+  const real e2[3] = {kh[1] * e1[2] - kh[2] * e1[1], kh[2] * e1[0] - kh[0] * e1[2], kh[0] * e1[1] - kh[1] * e1[0]};
   eps[0] = 0.0;
   for (int i = 0; i < 3; i++) eps[i + 1] = (which == 0) ? e1[i] : e2[i];
 }
@@ -334,12 +342,19 @@ int mgo_colour_matrix(int n, double* out /* complex [n!][n!] interleaved */) {
   const cplx* C = colour_matrix(n);
   if (!C) return MGO_ERR_NOMEM;
   const int np = factorial(n);
-  memcpy(out, C, sizeof(cplx) * np * np);
+  for (int i = 0; i < np * np; i++) {
+    out[2 * i] = (double)creal(C[i]);
+    out[2 * i + 1] = (double)cimag(C[i]);
+  }
   return MGO_OK;
 }
 
 int mgo_generators(double* out /* complex [8][3][3] */) {
-  memcpy(out, TGEN, sizeof(TGEN));
+  const cplx* t = &TGEN[0][0][0];
+  for (int i = 0; i < 72; i++) {
+    out[2 * i] = (double)creal(t[i]);
+    out[2 * i + 1] = (double)cimag(t[i]);
+  }
   return MGO_OK;
 }
 
@@ -349,17 +364,17 @@ int mgo_generators(double* out /* complex [8][3][3] */) {
 
 typedef struct {
   int n;                      /* number of gluons                         */
-  double k[MAXG][4];          /* incoming gluon momenta, by gluon index  */
+  real k[MAXG][4];          /* incoming gluon momenta, by gluon index  */
   cplx eps[MAXG][4];          /* gluon wavefunctions, by gluon index     */
-  double pt[4], ptb[4];       /* outgoing top / antitop momenta          */
+  real pt[4], ptb[4];       /* outgoing top / antitop momenta          */
   cplx ubar[4];               /* Dirac adjoint spinor of the top         */
   cplx v[4];                  /* spinor of the antitop                   */
-  double g, mt, wt;
+  real g, mt, wt;
 } qline;
 
 /* V3(a,b) = (Ja.Jb)(ka-kb) + Jb (2kb+ka).Ja - Ja (2ka+kb).Jb */
-static void vertex3(const double ka[4], const cplx ja[4], const double kb[4], const cplx jb[4], cplx out[4]) {
-  double x[4], y[4];
+static void vertex3(const real ka[4], const cplx ja[4], const real kb[4], const cplx jb[4], cplx out[4]) {
+  real x[4], y[4];
   for (int mu = 0; mu < 4; mu++) {
     x[mu] = 2.0 * kb[mu] + ka[mu];
     y[mu] = 2.0 * ka[mu] + kb[mu];
@@ -380,7 +395,7 @@ static void vertex4(const cplx l[4], const cplx m[4], const cplx r[4], cplx out[
 static cplx ordered_amplitude(const qline* q, const int* sigma) {
   const int n = q->n;
   cplx J[MAXG][MAXG][4];
-  double K[MAXG][MAXG][4];
+  real K[MAXG][MAXG][4];
   for (int i = 0; i < n; i++) {
     for (int mu = 0; mu < 4; mu++) {
       J[i][i][mu] = q->eps[sigma[i]][mu];
@@ -401,7 +416,7 @@ static cplx ordered_amplitude(const qline* q, const int* sigma) {
           vertex4(J[i][m1], J[m1 + 1][m2], J[m2 + 1][j], t);
           for (int mu = 0; mu < 4; mu++) acc[mu] += q->g * q->g * t[mu];
         }
-      const double p2 = dot_rr(K[i][j], K[i][j]);
+      const real p2 = dot_rr(K[i][j], K[i][j]);
       for (int mu = 0; mu < 4; mu++) J[i][j][mu] = acc[mu] / p2;
     }
   }
@@ -409,7 +424,7 @@ static cplx ordered_amplitude(const qline* q, const int* sigma) {
   cplx Psi[MAXG][4];
   for (int c = 0; c < 4; c++) Psi[0][c] = q->ubar[c];
   for (int k = 1; k < n; k++) {
-    double Q[4];
+    real Q[4];
     for (int mu = 0; mu < 4; mu++) Q[mu] = q->pt[mu] - K[0][k - 1][mu];
     const cplx den = dot_rr(Q, Q) - q->mt * q->mt + I * q->mt * q->wt;
     cplx row[4] = {0, 0, 0, 0}, t[4];
@@ -452,7 +467,7 @@ static int fill_qline(qline* q, int n, const double* params, const double* kin, 
   oparams o;
   unpack_params(params, &o);
   q->n = n;
-  q->g = sqrt(4.0 * M_PI * o.alpha_s);
+  q->g = sqrt(4.0 * PI_R * o.alpha_s);
   q->mt = o.mt;
   q->wt = o.wt;
   for (int i = 0; i < n; i++)
@@ -476,7 +491,12 @@ int mgo_ordered_amps(int n, const double* params, const double* kin, const doubl
   qline q;
   int rc = fill_qline(&q, n, params, kin, eps, pt, ubar, ptb, v);
   if (rc) return rc;
-  all_ordered_amplitudes(&q, (cplx*)amps_out);
+  cplx A[MAXPERM];
+  all_ordered_amplitudes(&q, A);
+  for (int i = 0; i < factorial(n); i++) {
+    amps_out[2 * i] = (double)creal(A[i]);
+    amps_out[2 * i + 1] = (double)cimag(A[i]);
+  }
   return MGO_OK;
 }
 
@@ -504,7 +524,7 @@ int mgo_ordered_colour_sum(int n, const double* params, const double* kin, const
 /* gluon subsets, summed over every colour assignment of the externals.*/
 /* ------------------------------------------------------------------ */
 
-static double FABC[8][8][8];
+static real FABC[8][8][8];
 static int fabc_ready = 0;
 static pthread_mutex_t fabc_lock = PTHREAD_MUTEX_INITIALIZER;
 
@@ -531,13 +551,14 @@ static void init_fabc(void) {
 
 int mgo_fabc(double* out /* [8][8][8] */) {
   init_fabc();
-  memcpy(out, FABC, sizeof(FABC));
+  const real* f = &FABC[0][0][0];
+  for (int i = 0; i < 512; i++) out[i] = (double)f[i];
   return MGO_OK;
 }
 
 typedef struct {
   cplx J[1 << MAXG][8][4]; /* J[subset][colour][mu] */
-  double K[1 << MAXG][4];
+  real K[1 << MAXG][4];
   int have[1 << MAXG];
 } dressed_ws;
 
@@ -555,7 +576,7 @@ static void dressed_current(const qline* q, const int* col, int S, dressed_ws* w
     w->have[S] = 1;
     return;
   }
-  const double g = q->g;
+  const real g = q->g;
   cplx acc[8][4];
   memset(acc, 0, sizeof(acc));
   /* three-gluon vertex: unordered splits {S1, S2}; S1 holds the lowest member of S */
@@ -570,7 +591,7 @@ static void dressed_current(const qline* q, const int* col, int S, dressed_ws* w
         cplx t[4];
         vertex3(w->K[S1], w->J[S1][a], w->K[S2], w->J[S2][b], t);
         for (int c = 0; c < 8; c++) {
-          const double f = FABC[a][b][c];
+          const real f = FABC[a][b][c];
           if (f == 0.0) continue;
           /* (-i/P^2) * g f^{abc} V3 */
           for (int mu = 0; mu < 4; mu++) acc[c][mu] += -I * g * f * t[mu];
@@ -600,7 +621,7 @@ static void dressed_current(const qline* q, const int* col, int S, dressed_ws* w
             const cplx d12 = dot_cc(j1, j2), d13 = dot_cc(j1, j3), d23 = dot_cc(j2, j3);
             if (d12 == 0 && d13 == 0 && d23 == 0) continue;
             for (int c = 0; c < 8; c++) {
-              double f1 = 0, f2 = 0, f3 = 0;
+              real f1 = 0, f2 = 0, f3 = 0;
               for (int e = 0; e < 8; e++) {
                 f1 += FABC[a][b][e] * FABC[d][c][e];
                 f2 += FABC[a][d][e] * FABC[b][c][e];
@@ -617,7 +638,7 @@ static void dressed_current(const qline* q, const int* col, int S, dressed_ws* w
           }
     }
   }
-  const double p2 = dot_rr(w->K[S], w->K[S]);
+  const real p2 = dot_rr(w->K[S], w->K[S]);
   for (int c = 0; c < 8; c++)
     for (int mu = 0; mu < 4; mu++) w->J[S][c][mu] = acc[c][mu] / p2;
   w->have[S] = 1;
@@ -637,7 +658,7 @@ int mgo_dressed_colour_sum(int n, const double* params, const double* kin, const
   int col[MAXG];
   long total = 1;
   for (int i = 0; i < n; i++) total *= 8;
-  double sum = 0.0;
+  real sum = 0.0;
   for (long code = 0; code < total; code++) {
     long c = code;
     for (int i = 0; i < n; i++) { col[i] = (int)(c % 8); c /= 8; }
@@ -649,7 +670,7 @@ int mgo_dressed_colour_sum(int n, const double* params, const double* kin, const
       for (int jo = 0; jo < 3; jo++)
         for (int s4 = 0; s4 < 4; s4++) Psi[0][it][jo][s4] = (it == jo) ? q.ubar[s4] : 0.0;
     for (int S = 1; S < full; S++) {
-      double Q[4];
+      real Q[4];
       for (int mu = 0; mu < 4; mu++) Q[mu] = q.pt[mu];
       for (int i = 0; i < n; i++)
         if (S & (1 << i))
@@ -714,27 +735,38 @@ int mgo_dressed_colour_sum(int n, const double* params, const double* kin, const
 /* External-state test hooks                                           */
 /* ------------------------------------------------------------------ */
 
+static void to_double_c(const cplx* in, int n, double* out) {
+  for (int i = 0; i < n; i++) {
+    out[2 * i] = (double)creal(in[i]);
+    out[2 * i + 1] = (double)cimag(in[i]);
+  }
+}
+
 int mgo_spinor(int kind /*0 u, 1 v, 2 ubar, 3 vbar*/, const double* p, double m, int s, double* out) {
   cplx w[4], b[4];
-  if (kind == 0 || kind == 2) spinor_u(p, m, s, w);
-  else spinor_v(p, m, s, w);
+  const real pr[4] = {p[0], p[1], p[2], p[3]};
+  if (kind == 0 || kind == 2) spinor_u(pr, m, s, w);
+  else spinor_v(pr, m, s, w);
   if (kind >= 2) {
     dirac_bar(w, b);
-    memcpy(out, b, sizeof(b));
+    to_double_c(b, 4, out);
   } else {
-    memcpy(out, w, sizeof(w));
+    to_double_c(w, 4, out);
   }
   return MGO_OK;
 }
 
 int mgo_polarisation(const double* k, int which, double* out) {
-  polarisation(k, which, out);
+  const real kr[4] = {k[0], k[1], k[2], k[3]};
+  real e[4];
+  polarisation(kr, which, e);
+  for (int i = 0; i < 4; i++) out[i] = (double)e[i];
   return MGO_OK;
 }
 
 int mgo_gamma(double* out /* complex [5][4][4]: gamma^0..3, gamma^5 */) {
-  memcpy(out, GAM, sizeof(GAM));
-  memcpy(out + 2 * 64, GAM5, sizeof(GAM5));
+  to_double_c(&GAM[0][0][0], 64, out);
+  to_double_c(&GAM5[0][0], 16, out + 2 * 64);
   return MGO_OK;
 }
 
@@ -743,22 +775,22 @@ int mgo_gamma(double* out /* complex [5][4][4]: gamma^0..3, gamma^5 */) {
 /* ------------------------------------------------------------------ */
 
 /* e+(p1) e-(p2) -> mu+(p3) mu-(p4) through s-channel photon and Z */
-static double me_eemumu(const oparams* o, const double* mom) {
-  const double* p1 = mom;
-  const double* p2 = mom + 4;
-  const double* p3 = mom + 8;
-  const double* p4 = mom + 12;
-  const double alpha = 1.0 / o->alpha_em_inv;
-  const double ee = sqrt(4.0 * M_PI * alpha);
-  const double mz2 = o->mz * o->mz;
-  const double mw2 = 0.5 * mz2 + sqrt(0.25 * mz2 * mz2 - M_PI * alpha * mz2 / (M_SQRT2 * o->gf));
-  const double sw2 = 1.0 - mw2 / mz2;
-  const double cw2 = 1.0 - sw2;
-  const double gl = -0.5 + sw2, gr = sw2;                /* T3 - Q sw^2 for Q = -1 */
-  const double gz = ee / sqrt(sw2 * cw2);
-  double ptot[4];
+static real me_eemumu(const oparams* o, const real* mom) {
+  const real* p1 = mom;
+  const real* p2 = mom + 4;
+  const real* p3 = mom + 8;
+  const real* p4 = mom + 12;
+  const real alpha = 1.0 / o->alpha_em_inv;
+  const real ee = sqrt(4.0 * PI_R * alpha);
+  const real mz2 = o->mz * o->mz;
+  const real mw2 = 0.5 * mz2 + sqrt(0.25 * mz2 * mz2 - PI_R * alpha * mz2 / (sqrt((real)2) * o->gf));
+  const real sw2 = 1.0 - mw2 / mz2;
+  const real cw2 = 1.0 - sw2;
+  const real gl = -0.5 + sw2, gr = sw2;                /* T3 - Q sw^2 for Q = -1 */
+  const real gz = ee / sqrt(sw2 * cw2);
+  real ptot[4];
   for (int mu = 0; mu < 4; mu++) ptot[mu] = p1[mu] + p2[mu];
-  const double s = dot_rr(ptot, ptot);
+  const real s = dot_rr(ptot, ptot);
   const cplx prop_a = -I / s;
   const cplx prop_z = o->photon_only ? 0.0 : -I / (s - mz2 + I * o->mz * o->wz);
   /* Gamma_gamma^mu = -i e Q gamma^mu (Q = -1); Gamma_Z^mu = -i gz gamma^mu (gl PL + gr PR) */
@@ -780,7 +812,7 @@ static double me_eemumu(const oparams* o, const double* mom) {
         GZ[mu][r][c] = -I * gz * tmp[r][c];
       }
   }
-  double sum = 0.0;
+  real sum = 0.0;
   for (int s1 = 0; s1 < 2; s1++)
     for (int s2 = 0; s2 < 2; s2++)
       for (int s3 = 0; s3 < 2; s3++)
@@ -811,7 +843,7 @@ static double me_eemumu(const oparams* o, const double* mom) {
 }
 
 /* g(p1) g(p2) -> t(p3) t~(p4) g(p5) ... : n gluons in total */
-static double me_ggtt_ng(const oparams* o, int n, const double* mom) {
+static real me_ggtt_ng(const oparams* o, int n, const real* mom) {
   const cplx* C = colour_matrix(n);
   if (!C) return NAN;
   const int np = factorial(n);
@@ -822,17 +854,17 @@ static double me_ggtt_ng(const oparams* o, int n, const double* mom) {
   for (int i = 2; i < n; i++) slot[i] = i + 2;
   qline q;
   q.n = n;
-  q.g = sqrt(4.0 * M_PI * o->alpha_s);
+  q.g = sqrt(4.0 * PI_R * o->alpha_s);
   q.mt = o->mt;
   q.wt = o->wt;
   for (int mu = 0; mu < 4; mu++) {
     q.pt[mu] = mom[8 + mu];
     q.ptb[mu] = mom[12 + mu];
   }
-  double pol[MAXG][2][4];
+  real pol[MAXG][2][4];
   for (int i = 0; i < n; i++) {
-    const double* p = mom + 4 * slot[i];
-    const double sign = (slot[i] < 2) ? 1.0 : -1.0; /* incoming momentum */
+    const real* p = mom + 4 * slot[i];
+    const real sign = (slot[i] < 2) ? 1.0 : -1.0; /* incoming momentum */
     for (int mu = 0; mu < 4; mu++) q.k[i][mu] = sign * p[mu];
     polarisation(p, 0, pol[i][0]);
     polarisation(p, 1, pol[i][1]);
@@ -844,7 +876,7 @@ static double me_ggtt_ng(const oparams* o, int n, const double* mom) {
     dirac_bar(u, ubar_s[s]);
     spinor_v(q.ptb, o->mt, s, v_s[s]);
   }
-  double sum = 0.0;
+  real sum = 0.0;
   cplx A[MAXPERM];
   const int nhel = 1 << (n + 2);
   for (int h = 0; h < nhel; h++) {
@@ -861,7 +893,7 @@ static double me_ggtt_ng(const oparams* o, int n, const double* mom) {
       for (int j = 0; j < np; j++) s += conj(A[i]) * C[i * np + j] * A[j];
     sum += creal(s);
   }
-  double iden = 4.0 * 64.0;
+  real iden = 4.0 * 64.0;
   for (int i = 2; i <= n - 2; i++) iden *= i; /* identical final-state gluons */
   return sum / iden;
 }
@@ -890,8 +922,9 @@ int mgo_me(int proc, const double* params, const double* mom, int64_t nevt, doub
   if (npar < 0 || nevt < 0) return MGO_ERR_ARG;
   if (proc != MGO_EEMUMU && !colour_matrix(proc_gluons(proc))) return MGO_ERR_NOMEM;
   for (int64_t e = 0; e < nevt; e++) {
-    const double* p = mom + (size_t)e * npar * 4;
-    me[e] = (proc == MGO_EEMUMU) ? me_eemumu(&o, p) : me_ggtt_ng(&o, proc_gluons(proc), p);
+    real p[4 * (MAXG + 2)];
+    for (int i = 0; i < npar * 4; i++) p[i] = mom[(size_t)e * npar * 4 + i];
+    me[e] = (double)((proc == MGO_EEMUMU) ? me_eemumu(&o, p) : me_ggtt_ng(&o, proc_gluons(proc), p));
   }
   return MGO_OK;
 }

@@ -78,26 +78,29 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr uint32_t WAIT_POLLS = 1u << 22;
 
 // ---------------------------------------------------------------------------
-// shared-memory layout: [mbarriers 128 B][momenta tile][per-thread slab]
+// shared-memory layout:
+//   [mbarriers 128 B][momenta tile][per-thread slab [NSLOT][NT]][colour flows [NCOL][NT]]
+// Each thread reads and writes only its own column of the slab and of the
+// colour-flow accumulators, so the helicity loop needs no block barrier.
 // ---------------------------------------------------------------------------
 template <class P, typename R, int NT>
 struct Layout {
   static constexpr size_t bar_bytes = 128;
   static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
   static constexpr size_t slab_bytes = size_t(NT) * P::NSLOT * sizeof(R);
+  static constexpr size_t jamp_bytes = size_t(NT) * P::NCOL * sizeof(cx<R>);
   static constexpr size_t slab_off = bar_bytes + ((stage_bytes + 127) / 128) * 128;
-  static constexpr size_t base_bytes = slab_off + ((slab_bytes + 127) / 128) * 128;
+  static constexpr size_t jamp_off = slab_off + ((slab_bytes + 127) / 128) * 128;
+  static constexpr size_t base_bytes = jamp_off + ((jamp_bytes + 127) / 128) * 128;
 };
 
 // A1 + A2: stage the tile, run the per-event FP64 set-up into the slab.
-// Returns the number of valid events in the tile, or -1 after a timed-out copy.
+// Returns the number of valid events in the tile, or -1 after a timed-out copy
+// (uniformly for the whole CTA).
 template <class P, typename R, int NT>
-__device__ __forceinline__ int load_and_prepare(unsigned char* smem, const double* __restrict__ mom, long long nevt,
-                                                const KParams& kp, unsigned* status) {
-  using LY = Layout<P, R, NT>;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  double* stage = reinterpret_cast<double*>(smem + LY::bar_bytes);
-  R* slab = reinterpret_cast<R*>(smem + LY::slab_off);
+__device__ __forceinline__ int load_and_prepare_at(uint64_t* bar, double* stage, R* slab,
+                                                   const double* __restrict__ mom, long long nevt,
+                                                   const KParams& kp, unsigned* status) {
   const int tid = threadIdx.x;
   const long long e0 = (long long)blockIdx.x * NT;
   const long long rem = nevt - e0;
@@ -111,7 +114,8 @@ __device__ __forceinline__ int load_and_prepare(unsigned char* smem, const doubl
     bulk_g2s(stage, mom + e0 * P::NPAR * 4, bytes, bar);
   }
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0, WAIT_POLLS)) {
+  // the outcome of the bounded wait is made uniform across the CTA
+  if (!__syncthreads_and(mbar_wait_bounded(bar, 0, WAIT_POLLS) ? 1 : 0)) {
     // the copy did not complete: flag it, wait once more (bounded) so that no
     // copy is left in flight into this CTA's shared memory, and give up
     if (tid == 0) atomicOr(status, ST_TMA_TIMEOUT);
@@ -121,6 +125,15 @@ __device__ __forceinline__ int load_and_prepare(unsigned char* smem, const doubl
   const int le = tid < nvalid ? tid : nvalid - 1;  // ragged tail: repeat a valid event
   P::template prepare<R>(stage + le * P::NPAR * 4, kp.v, slab + tid, NT);
   return nvalid;
+}
+
+template <class P, typename R, int NT>
+__device__ __forceinline__ int load_and_prepare(unsigned char* smem, const double* __restrict__ mom, long long nevt,
+                                                const KParams& kp, unsigned* status) {
+  using LY = Layout<P, R, NT>;
+  return load_and_prepare_at<P, R, NT>(reinterpret_cast<uint64_t*>(smem),
+                                       reinterpret_cast<double*>(smem + LY::bar_bytes),
+                                       reinterpret_cast<R*>(smem + LY::slab_off), mom, nevt, kp, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -135,12 +148,13 @@ __global__ void __launch_bounds__(NT) sigma_kernel(const double* __restrict__ mo
   const int nvalid = load_and_prepare<P, R, NT>(smem, mom, nevt, kp, status);
   if (nvalid < 0) return;
   const R* ev = reinterpret_cast<const R*>(smem + LY::slab_off) + threadIdx.x;
+  cx<R>* jamp = reinterpret_cast<cx<R>*>(smem + LY::jamp_off) + threadIdx.x;
   double acc = 0.0;
+#pragma unroll 1
   for (int ih = 0; ih < nhel; ih++) {
     const int h = __ldg(hels + ih);
-    cx<R> jamp[P::NCOL];
-    P::template amplitudes<R>(ev, NT, h, kp.v, jamp);
-    acc += (double)P::template colour_quadratic<R>(jamp);
+    P::template amplitudes<R>(ev, NT, h, kp.v, jamp, NT);
+    acc += (double)P::template colour_quadratic<R>(jamp, NT);
   }
   if ((int)threadIdx.x < nvalid) {
     constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
@@ -158,12 +172,13 @@ __global__ void __launch_bounds__(NT) helicity_kernel(const double* __restrict__
   const int nvalid = load_and_prepare<P, double, NT>(smem, mom, nevt, kp, status);
   if (nvalid < 0) return;
   const double* ev = reinterpret_cast<const double*>(smem + LY::slab_off) + threadIdx.x;
+  cx<double>* jamp = reinterpret_cast<cx<double>*>(smem + LY::jamp_off) + threadIdx.x;
   const long long e = (long long)blockIdx.x * NT + threadIdx.x;
   constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+#pragma unroll 1
   for (int h = 0; h < P::NHEL; h++) {
-    cx<double> jamp[P::NCOL];
-    P::template amplitudes<double>(ev, NT, h, kp.v, jamp);
-    const double v = P::template colour_quadratic<double>(jamp) * norm;
+    P::template amplitudes<double>(ev, NT, h, kp.v, jamp, NT);
+    const double v = P::template colour_quadratic<double>(jamp, NT) * norm;
     if ((int)threadIdx.x < nvalid) out[e * P::NHEL + h] = v;
   }
 }
@@ -178,6 +193,7 @@ struct LaunchArgs {
   const int* hels;
   int nhel;
   KParams kp;
+  const void* ctile;  // FP16 colour-matrix operand tile (tensor-core path)
   unsigned* status;
   cudaStream_t stream;
 };
@@ -221,6 +237,7 @@ struct ProcDesc {
   int (*sigma_fp64)(const LaunchArgs&);
   int (*sigma_mixed)(const LaunchArgs&);
   int (*helicities)(const LaunchArgs&);
+  int tc_k;  // > 0: the mixed path contracts colour on the tensor cores, K = N = tc_k
 };
 
 }  // namespace mg

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "mg.h"
+#include "mg_colour_tc.cuh"
 #include "mg_kernels.cuh"
 #include "mg_runtime_internal.h"
 
@@ -123,6 +124,22 @@ extern "C" int mg_process_create(const char* proc, const mg_params* p, mg_proces
     return MG_ERR_CUDA;
   }
   h->n_good = d->nhel;
+  if (p->precision == MG_MIXED && d->tc_k > 0) {
+    // FP16 operand image of the colour matrix for the tensor-core colour sum
+    std::vector<unsigned short> tile((size_t)d->tc_k * d->tc_k);
+    if (!mg::colour_tile_host(d->knum, d->ncol, tile.data())) {
+      mg_process_destroy(h);
+      return MG_ERR_STATE;  // a colour numerator is not exact in FP16
+    }
+    if (cudaMalloc(&h->d_ctile, tile.size() * 2) != cudaSuccess) {
+      mg_process_destroy(h);
+      return MG_ERR_NOMEM;
+    }
+    if (cudaMemcpy(h->d_ctile, tile.data(), tile.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+      mg_process_destroy(h);
+      return MG_ERR_CUDA;
+    }
+  }
   // one-time kernel attributes (no launch for nevt = 0), so that later calls
   // can be captured into CUDA graphs
   LaunchArgs a{};
@@ -142,6 +159,7 @@ extern "C" void mg_process_destroy(mg_process* h) {
   cudaFree(h->d_hels);
   for (int* p : h->old_hels) cudaFree(p);
   cudaFree(h->d_status);
+  cudaFree(h->d_ctile);
   cudaFree(h->d_mom);
   cudaFree(h->d_me);
   delete h;
@@ -165,6 +183,7 @@ int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, 
   a.hels = h->d_hels;
   a.nhel = h->n_good;
   a.kp = h->kp;
+  a.ctile = h->d_ctile;
   a.status = h->d_status;
   a.stream = stream;
   const int rc = (h->par.precision == MG_MIXED) ? h->d->sigma_mixed(a) : h->d->sigma_fp64(a);

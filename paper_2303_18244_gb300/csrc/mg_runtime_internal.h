@@ -20,6 +20,7 @@ struct mg_process {
   unsigned hel_version = 0;         // bumped when the helicity list changes
   std::vector<uint8_t> mask;
   unsigned* d_status = nullptr;     // device status word (bounded-wait timeouts)
+  void* d_ctile = nullptr;          // FP16 colour-matrix operand tile (mixed, tensor cores)
   std::mutex lock;
   // workspace of mg_sigma_host
   std::mutex ws_lock;

@@ -19,6 +19,13 @@
 #include <math.h>
 #include <stdint.h>
 
+// MG_VERTEX: inlining of the vertex routines (ffv_*, vvv_*, vvvv_*).  Inlined
+// by default; a translation unit may define it as __noinline__ to compile very
+// large processes as a sequence of calls.
+#ifndef MG_VERTEX
+#define MG_VERTEX __forceinline__
+#endif
+
 namespace mg {
 
 template <typename R>
@@ -288,7 +295,7 @@ __device__ __forceinline__ void mulcol(const cx<R> M[4], cx<R> c0, cx<R> c1, cx<
 
 // Fbar Jslash F
 template <typename R>
-__device__ __forceinline__ cx<R> ffv_amp(const Sp<R>& a, const V4<R>& J, const Sp<R>& b) {
+__device__ MG_VERTEX cx<R> ffv_amp(const Sp<R>& a, const V4<R>& J, const Sp<R>& b) {
   cx<R> X[4], Y[4];
   sigma_blocks(J, X, Y);
   cx<R> t0, t1, u0, u1;
@@ -299,7 +306,7 @@ __device__ __forceinline__ cx<R> ffv_amp(const Sp<R>& a, const V4<R>& J, const S
 
 // row current: coef * Fbar Jslash (Qslash + m)
 template <typename R>
-__device__ __forceinline__ Sp<R> ffv_row(const Sp<R>& a, const V4<R>& J, const R Q[4], R m, cx<R> coef) {
+__device__ MG_VERTEX Sp<R> ffv_row(const Sp<R>& a, const V4<R>& J, const R Q[4], R m, cx<R> coef) {
   cx<R> X[4], Y[4], XQ[4], YQ[4];
   sigma_blocks(J, X, Y);
   sigma_blocks(Q, XQ, YQ);
@@ -319,7 +326,7 @@ __device__ __forceinline__ Sp<R> ffv_row(const Sp<R>& a, const V4<R>& J, const R
 
 // column current: coef * (qslash + m) Jslash F
 template <typename R>
-__device__ __forceinline__ Sp<R> ffv_col(const V4<R>& J, const Sp<R>& b, const R q[4], R m, cx<R> coef) {
+__device__ MG_VERTEX Sp<R> ffv_col(const V4<R>& J, const Sp<R>& b, const R q[4], R m, cx<R> coef) {
   cx<R> X[4], Y[4], XQ[4], YQ[4];
   sigma_blocks(J, X, Y);
   sigma_blocks(q, XQ, YQ);
@@ -339,7 +346,7 @@ __device__ __forceinline__ Sp<R> ffv_col(const V4<R>& J, const Sp<R>& b, const R
 
 // vector current coef * Fbar gamma^mu (cL PL + cR PR) F
 template <typename R>
-__device__ __forceinline__ V4<R> ffv_vcur(const Sp<R>& a, const Sp<R>& b, cx<R> coef, R cL = R(1), R cR = R(1)) {
+__device__ MG_VERTEX V4<R> ffv_vcur(const Sp<R>& a, const Sp<R>& b, cx<R> coef, R cL = R(1), R cR = R(1)) {
   // upper: (a0,a1) sigma^mu (b2,b3) [right-handed F], lower: (a2,a3) sigmabar^mu (b0,b1)
   const cx<R> u02 = a.c[0] * b.c[2], u13 = a.c[1] * b.c[3], u03 = a.c[0] * b.c[3], u12 = a.c[1] * b.c[2];
   const cx<R> l20 = a.c[2] * b.c[0], l31 = a.c[3] * b.c[1], l21 = a.c[2] * b.c[1], l30 = a.c[3] * b.c[0];
@@ -355,7 +362,7 @@ __device__ __forceinline__ V4<R> ffv_vcur(const Sp<R>& a, const Sp<R>& b, cx<R> 
 // three-gluon current: c * V3(kx, Jx, ky, Jy),
 //   V3 = (Jx.Jy)(kx-ky) + Jy (2ky+kx).Jx - Jx (2kx+ky).Jy
 template <typename R>
-__device__ __forceinline__ V4<R> vvv_cur(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy, R c) {
+__device__ MG_VERTEX V4<R> vvv_cur(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy, R c) {
   R a[4], b[4];
   for (int mu = 0; mu < 4; mu++) {
     a[mu] = R(2) * ky[mu] + kx[mu];
@@ -375,7 +382,7 @@ __device__ __forceinline__ V4<R> vvv_cur(const R kx[4], const V4<R>& Jx, const R
 }
 // amplitude: c * V3(kx, Jx, ky, Jy) . G
 template <typename R>
-__device__ __forceinline__ cx<R> vvv_amp(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy,
+__device__ MG_VERTEX cx<R> vvv_amp(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy,
                                          const V4<R>& G, R c) {
   R a[4], b[4], d[4];
   for (int mu = 0; mu < 4; mu++) {
@@ -391,7 +398,7 @@ __device__ __forceinline__ cx<R> vvv_amp(const R kx[4], const V4<R>& Jx, const R
 // four-gluon Lorentz structures for the three colour branches
 //   br 0: (X.Z) Y - (Y.Z) X     br 1: (X.Y) Z - (Y.Z) X     br 2: (X.Y) Z - (X.Z) Y
 template <int BR, typename R>
-__device__ __forceinline__ V4<R> vvvv_cur(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, R c) {
+__device__ MG_VERTEX V4<R> vvvv_cur(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, R c) {
   V4<R> o;
   if (BR == 0) {
     const cx<R> xz = dot(X, Z), yz = dot(Y, Z);
@@ -406,7 +413,7 @@ __device__ __forceinline__ V4<R> vvvv_cur(const V4<R>& X, const V4<R>& Y, const 
   return o;
 }
 template <int BR, typename R>
-__device__ __forceinline__ cx<R> vvvv_amp(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, const V4<R>& G, R c) {
+__device__ MG_VERTEX cx<R> vvvv_amp(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, const V4<R>& G, R c) {
   cx<R> t;
   if (BR == 0) t = dot(X, Z) * dot(Y, G) - dot(Y, Z) * dot(X, G);
   else if (BR == 1) t = dot(X, Y) * dot(Z, G) - dot(Y, Z) * dot(X, G);

@@ -7,11 +7,11 @@ For every process the generated header defines, as struct mg::<tag>:
                                      as R in the per-thread slab ev[k*es]:
                                      external-state ingredients, propagator
                                      coefficients (-g/P^2, -g/(P^2-m^2+i m G))
-  amplitudes<R>(ev, es, hel, kp, jamp)  per helicity: external wavefunctions,
+  amplitudes<R>(ev, es, hel, kp, jamp, js)  per helicity: external wavefunctions,
                                      off-shell currents and amplitudes diagram
                                      by diagram, accumulated into the colour
-                                     flows jamp[NCOL]
-  colour_quadratic<R>(jamp)          sum_ij KNUM_ij Re/Im(J_i) Re/Im(J_j)
+                                     flows jamp[k * js], k < NCOL
+  colour_quadratic<R>(jamp, js)          sum_ij KNUM_ij Re/Im(J_i) Re/Im(J_j)
                                      (C = KNUM / CDEN)
 
 Helicity index convention: particle i has helicity +1 when bit (NPAR-1-i) of
@@ -56,15 +56,15 @@ def _colour_quadratic(K, ncol) -> list[str]:
             k = K[i][j] if j == i else 2 * K[i][j]
             if k == 0:
                 continue
-            terms_r.append((k, f"jamp[{j}].re"))
-            terms_i.append((k, f"jamp[{j}].im"))
+            terms_r.append((k, f"JAMP({j}).re"))
+            terms_i.append((k, f"JAMP({j}).im"))
         if not terms_r:
             continue
         k0, v0 = terms_r[0]
         out.append(f"  {{ R yr = R({k0}) * {v0}; R yi = R({k0}) * {terms_i[0][1]};")
         for (k, vr), (_, vi) in zip(terms_r[1:], terms_i[1:]):
             out.append(f"    yr = fmaf_t<R>(R({k}), {vr}, yr); yi = fmaf_t<R>(R({k}), {vi}, yi);")
-        out.append(f"    acc = fmaf_t<R>(jamp[{i}].re, yr, acc); acc = fmaf_t<R>(jamp[{i}].im, yi, acc); }}")
+        out.append(f"    acc = fmaf_t<R>(JAMP({i}).re, yr, acc); acc = fmaf_t<R>(JAMP({i}).im, yi, acc); }}")
     out.append("  return acc;")
     return out
 
@@ -177,13 +177,15 @@ def emit_gg(n: int, tag: str) -> str:
     L.append("// one helicity: currents and amplitudes, diagram by diagram, into the colour flows")
     L.append("template <typename R>")
     L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
-    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp) {")
+    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp,")
+    L.append("                                           const int js) {")
     L.append("#define EV(k) ev[(k) * es]")
+    L.append("#define JAMP(k) jamp[(k) * js]")
     L.append("  const R g = R(kp[0]);")
     L.append("  const R mt = R(kp[1]);")
     for i in range(npar):
         L.append(f"  const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
-    L.append(f"  for (int c = 0; c < {ncol}; c++) jamp[c] = {{R(0), R(0)}};")
+    L.append(f"  for (int c = 0; c < {ncol}; c++) JAMP(c) = cx<R>{{R(0), R(0)}};")
     # momenta (R) on demand
     emitted_k = set()
 
@@ -261,13 +263,8 @@ def emit_gg(n: int, tag: str) -> str:
         emitted[cid] = name
         return name
 
-    # order amplitudes so that those sharing late currents are adjacent
-    def deps(op):
-        return op[1:4] if op[0] != "a4" else op[1:4]
-
-    order = sorted(range(len(plan.amps)), key=lambda i: (max(deps(plan.amps[i][0])), i))
     gtt_id = plan.keys.get(("gtt",))
-    for ai in order:
+    for ai in schedule(plan):
         op, co = plan.amps[ai]
         if op[0] == "f":
             r, gq, c = cur(op[1]), cur(op[2]), cur(op[3])
@@ -287,23 +284,128 @@ def emit_gg(n: int, tag: str) -> str:
         parts = []
         for k, c in sorted(co.items()):
             if c == 1:
-                parts.append(f"jamp[{k}] = jamp[{k}] + a;")
+                parts.append(f"JAMP({k}) = JAMP({k}) + a;")
             elif c == -1:
-                parts.append(f"jamp[{k}] = jamp[{k}] - a;")
+                parts.append(f"JAMP({k}) = JAMP({k}) - a;")
             else:
-                parts.append(f"jamp[{k}] = fma(R({c}), a, jamp[{k}]);")
+                parts.append(f"JAMP({k}) = fma(R({c}), a, JAMP({k}));")
         L.append("    " + " ".join(parts) + " }")
+    L.append("#undef JAMP")
     L.append("#undef EV")
     L.append("}")
     L.append("")
     L.append("// sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j); |M|^2 colour sum = result / CDEN")
     L.append("template <typename R>")
-    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp) {")
+    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
+    L.append("#define JAMP(k) jamp[(k) * js]")
     L.extend(_colour_quadratic(K, ncol))
+    L.append("#undef JAMP")
     L.append("}")
     L.append(f"}};  // struct {tag}")
     L.append("}  // namespace mg")
     return "\n".join(L) + "\n"
+
+
+def current_deps(plan, cid) -> list[int]:
+    """Currents that current cid reads."""
+    op = plan.ops[cid]
+    k = op[0]
+    if k == "3":
+        return [op[1], op[2]]
+    if k == "4":
+        return [op[1], op[2], op[3]]
+    if k == "row":
+        return [op[1], op[2]]
+    if k == "col":
+        return [op[1], op[2]]
+    if k == "gtt":
+        return [plan.keys[("row", ())], plan.keys[("col", ())]]
+    return []
+
+
+def amp_deps(plan, op) -> list[int]:
+    gtt = plan.keys.get(("gtt",))
+    if op[0] == "f":
+        return [op[1], op[2], op[3]]
+    if op[0] == "a3":
+        return [op[1], op[2], gtt]
+    return [op[1], op[2], op[3], gtt]
+
+
+def schedule(plan) -> list[int]:
+    """Order of the amplitudes for emission (currents are emitted on first use).
+
+    Greedy list scheduling against register pressure: at every step take the
+    amplitude minimising (currents it still has to create) - (currents whose
+    last use it is), preferring amplitudes that touch already-live currents.
+    """
+    namp = len(plan.amps)
+    adeps = [amp_deps(plan, op) for op, _ in plan.amps]
+    cdeps = [current_deps(plan, c) for c in range(len(plan.ops))]
+    remaining = [0] * len(plan.ops)
+    users = [[] for _ in plan.ops]
+    for c in range(len(plan.ops)):
+        for d in cdeps[c]:
+            remaining[d] += 1
+    for a in range(namp):
+        for d in adeps[a]:
+            remaining[d] += 1
+            users[d].append(a)
+    for c in range(len(plan.ops)):
+        for d in cdeps[c]:
+            users[d].append(("c", c))
+    computed = [False] * len(plan.ops)
+    done = [False] * namp
+    order = []
+
+    def need_of(a):
+        need = []
+        seen = set()
+
+        def visit(c):
+            if computed[c] or c in seen:
+                return
+            seen.add(c)
+            for d in cdeps[c]:
+                visit(d)
+            need.append(c)
+        for d in adeps[a]:
+            visit(d)
+        return need
+
+    def score(a):
+        need = need_of(a)
+        use = {}
+        for c in need:
+            for d in cdeps[c]:
+                use[d] = use.get(d, 0) + 1
+        for d in adeps[a]:
+            use[d] = use.get(d, 0) + 1
+        freed = sum(1 for d, u in use.items() if remaining[d] - u == 0)
+        return len(need) - freed, need
+
+    live_amps = set()
+    while len(order) < namp:
+        cands = [a for a in live_amps if not done[a]] or [next(a for a in range(namp) if not done[a])]
+        best = None
+        for a in cands:
+            sc, need = score(a)
+            if best is None or (sc, a) < (best[0], best[1]):
+                best = (sc, a, need)
+        _, a, need = best
+        for c in need:
+            computed[c] = True
+            for d in cdeps[c]:
+                remaining[d] -= 1
+            for u in users[c]:
+                if not isinstance(u, tuple):
+                    live_amps.add(u)
+        for d in adeps[a]:
+            remaining[d] -= 1
+        done[a] = True
+        live_amps.discard(a)
+        order.append(a)
+    return order
 
 
 def _mask_of(plan, cid) -> int:
@@ -353,7 +455,8 @@ def emit_eemumu(tag: str) -> str:
     L.append("}")
     L.append("template <typename R>")
     L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
-    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp) {")
+    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp,")
+    L.append("                                           const int js) {")
     L.append("#define EV(k) ev[(k) * es]")
     L.append("#define ING(i) FermIngr<R>{EV(5 * (i)), EV(5 * (i) + 1), EV(5 * (i) + 2), EV(5 * (i) + 3), EV(5 * (i) + 4)}")
     for i in range(4):
@@ -375,7 +478,7 @@ def emit_eemumu(tag: str) -> str:
     L.append("#undef EV")
     L.append("}")
     L.append("template <typename R>")
-    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp) {")
+    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
     L.append("  return jamp[0].re * jamp[0].re + jamp[0].im * jamp[0].im;")
     L.append("}")
     L.append(f"}};  // struct {tag}")
@@ -401,21 +504,31 @@ THREADS = {
 }
 
 
+# processes whose mixed path contracts colour on the tensor cores (the FP16
+# operand tiles of 128 events plus FP32 colour-flow accumulators must fit in
+# shared memory next to the per-event slab)
+TENSOR_CORE_COLOUR = {"ggttg", "ggttgg"}
+
+
 def emit_kernels_tu(proc: str) -> tuple[str, str]:
     """Translation unit instantiating the kernels of one process."""
     tag, _ = PROCESSES[proc]
     nt64, nt32 = THREADS[tag]
+    tc = tag in TENSOR_CORE_COLOUR
+    mixed = f"launch_sigma_tc<{tag}>(a)" if tc else f"launch_sigma<{tag}, float, {nt32}>(a)"
+    tck = f"tc::pad16({tag}::NCOL)" if tc else "0"
     src = f"""// generated by paper_2303_18244_gb300.generator: kernels of '{proc}'
 #include "../mg_kernels.cuh"
+#include "../mg_colour_tc.cuh"
 #include "{tag}.cuh"
 
 namespace mg {{
 static int sigma_fp64(const LaunchArgs& a) {{ return launch_sigma<{tag}, double, {nt64}>(a); }}
-static int sigma_mixed(const LaunchArgs& a) {{ return launch_sigma<{tag}, float, {nt32}>(a); }}
+static int sigma_mixed(const LaunchArgs& a) {{ return {mixed}; }}
 static int helicities(const LaunchArgs& a) {{ return launch_helicities<{tag}, {nt64}>(a); }}
 static const ProcDesc desc = {{"{proc}", "{tag}", {tag}::NPAR, {tag}::NHEL, {tag}::NCOL, {tag}::NDIAG,
                               {tag}::NAMP, {tag}::IDEN, {tag}::CDEN, {tag}::KNUM,
-                              sigma_fp64, sigma_mixed, helicities}};
+                              sigma_fp64, sigma_mixed, helicities, {tck}}};
 const ProcDesc* proc_{tag}() {{ return &desc; }}
 }}  // namespace mg
 """

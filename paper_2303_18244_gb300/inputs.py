@@ -125,11 +125,14 @@ def rambo(sqrt_s: float, masses, u: np.ndarray) -> np.ndarray:
     p[..., 1:] = x[:, None, None] * (
         q[..., 1:] + b[:, None, :] * q[..., 0:1] + a[:, None, None] * bq[..., None] * b[:, None, :]
     )
-    # The massless conformal map leaves |E - |p|| at the rounding level of the
-    # boost, which grows with its gamma factor.  The rescaling step below is
-    # applied in every case (for massless final states it is a single exact
-    # step, xi = sqrt_s / sum |p|): energies are then recomputed from the
-    # 3-momenta, so every momentum is on its mass shell to rounding.
+    # The conformal map leaves the 3-momentum sum and |E - |p|| at the rounding
+    # level of its boost, which grows with the boost's gamma factor (up to
+    # ~1e-12 relative).  The residual 3-momentum sum is removed evenly, and the
+    # rescaling step below is applied in every case (for massless final
+    # states it is a single exact step, xi = sqrt_s / sum |p|): it keeps the
+    # zero sum and recomputes the energies from the 3-momenta, so the momenta
+    # conserve 4-momentum and sit on their mass shells to rounding.
+    p[..., 1:] -= p[..., 1:].sum(axis=1, keepdims=True) / nf
     if masses.sum() >= sqrt_s:
         raise ValueError("sqrt_s below the final-state mass threshold")
     p3sq = (p[..., 1:] ** 2).sum(axis=2)  # [nevt, nf]

@@ -62,6 +62,20 @@ def _rel(x, y):
     return np.abs(x - y) / np.abs(y)
 
 
+def _assert_fp64(proc, p, got, ref, tol=1e-12, params=None):
+    """Per-event relative error <= tol against the FP64 oracle; where the two
+    disagree by more, the long-double build of the oracle decides: the CUDA
+    result must then be within tol of the extended-precision value."""
+    r = _rel(got, ref)
+    bad = np.nonzero(r > tol)[0]
+    if bad.size:
+        ext = O.me(proc, p[bad], params, extended=True)
+        r_ext = _rel(got[bad], ext)
+        assert r_ext.max() <= tol, (
+            f"{bad.size} events beyond {tol:g}; vs extended precision max {r_ext.max():.3e} "
+            f"at event {int(bad[r_ext.argmax()])}")
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
     if not torch.cuda.is_available():
@@ -77,9 +91,8 @@ def test_fp64_parity_small(proc):
     h = mg.Process(proc)
     got = _gpu_me(h, p)
     ref = O.me(proc, p)
-    r = _rel(got, ref)
     assert np.all(np.isfinite(got))
-    assert r.max() <= 1e-12, f"max rel err {r.max():.3e} at event {int(r.argmax())}"
+    _assert_fp64(proc, p, got, ref)
 
 
 @pytest.mark.parametrize("proc", PROCS, ids=_ids)
@@ -117,7 +130,7 @@ def test_full_size_sampled(proc, precision):
     ref = O.me(proc, p[idx])
     r = _rel(got[idx], ref)
     if precision == mg.MG_FP64:
-        assert r.max() <= 1e-12, f"max rel err {r.max():.3e}"
+        _assert_fp64(proc, p[idx], got[idx], ref)
     else:
         assert np.median(r) <= 1e-5 and r.max() <= 1e-2
 
@@ -165,7 +178,7 @@ def test_ragged_sizes(n):
     p = process_momenta(proc, 1200.0, n, 17)
     h = mg.Process(proc)
     got = _gpu_me(h, p)
-    np.testing.assert_allclose(got, O.me(proc, p), rtol=1e-12)
+    _assert_fp64(proc, p, got, O.me(proc, p))
 
 
 def test_zero_events_and_bad_arguments():
@@ -201,7 +214,8 @@ def test_no_top_width_flag_matches_oracle():
     proc = "g g > t t~ g"
     p = process_momenta(proc, 1200.0, 200, 29)
     h = mg.Process(proc, flags=mg.MG_NO_TOP_WIDTH)
-    np.testing.assert_allclose(_gpu_me(h, p), O.me(proc, p, O.Params(wt=0.0)), rtol=1e-12)
+    par = O.Params(wt=0.0)
+    _assert_fp64(proc, p, _gpu_me(h, p), O.me(proc, p, par), params=par)
 
 
 def test_photon_only_closed_form():

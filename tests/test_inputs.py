@@ -31,7 +31,8 @@ def test_rambo_conservation_and_shell(proc, sqrts, mt):
     p = process_momenta(proc, sqrts, 500, 11, mt=mt)
     tot_in = p[:, :2].sum(axis=1)
     tot_out = p[:, 2:].sum(axis=1)
-    assert np.allclose(tot_in, tot_out, rtol=0, atol=1e-9 * sqrts)
+    # 4-momentum conserved to rounding (the imbalance of the conformal map is removed)
+    assert np.allclose(tot_in, tot_out, rtol=0, atol=2e-15 * sqrts)
     m2 = p[..., 0] ** 2 - (p[..., 1:] ** 2).sum(-1)
     want = np.zeros(p.shape[1])
     if "t t~" in proc:
