@@ -304,6 +304,10 @@ def serve_bench(args, mg, process_momenta):
     out = {}
     for prec_name, prec in (("mixed", mg.MG_MIXED), ("fp64", mg.MG_FP64)):
         handles = {p: mg.Process(p, precision=prec) for p in SERVE_PROCS}
+        for p, hh in handles.items():
+            calib = process_momenta(p, SERVE_PROCS[p], 1024, 1005)
+            import torch
+            mg.good_helicities(hh, torch.from_numpy(calib).cuda())
         u = uniforms(5, 0, args.serve_requests, 1)[:, 0, :]
         reqs = []
         for i in range(args.serve_requests):
