@@ -123,6 +123,34 @@ int mg_process_status(mg_process* h);
  * out_dev[nevt][n_hel].  Stream-ordered.  Diagnostics and helicity selection. */
 int mg_sigma_helicities(mg_process* h, const double* momenta_dev, int64_t nevt, double* out_dev, void* stream);
 
+/* Helicity filter that allocates nothing.  The paper has no counterpart: this
+ * is a library-usage variant of mg_good_helicities for callers that cannot
+ * call cudaMalloc -- code that runs under a fixed device-memory budget or its
+ * own pool allocator, where a stray allocation fails or fragments the pool,
+ * and latency-critical set-up paths that must not pay for cudaMalloc/cudaFree
+ * (which may synchronise the device).  Same result as mg_good_helicities
+ * (same threshold, same outputs), but its scratch (per-event, per-helicity
+ * values and the per-helicity reduction) lives in one file-scope device array
+ * of MG_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU loading the
+ * library holds until the process exits; the helicity list is rewritten in
+ * place in the handle.
+ *   - Limits: n_hel <= MG_STATIC_MAX_HEL and
+ *     nevt * n_hel <= MG_STATIC_SCRATCH_DOUBLES - MG_STATIC_MAX_HEL
+ *     (e.g. 8191 events for 128 helicities); larger requests return
+ *     MG_ERR_ARG without touching the device.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the array and it keeps the last call's contents (the
+ *     reduction slots are cleared at the start of each call).  Calls that
+ *     overlap on the GPU -- from several host threads, or with any other use
+ *     of the array -- race; serialise them.  The call synchronises the device
+ *     first, so no launch of this handle may be pending in another thread.
+ *   - Synchronous; runs on the legacy default stream. */
+#define MG_STATIC_SCRATCH_DOUBLES (1 << 20)
+#define MG_STATIC_MAX_HEL 128
+int mg_good_helicities_static(mg_process* h, const double* momenta_dev, int64_t nevt, int* n_good_out,
+                              uint8_t* mask_host);
+
 /* ---------------------------------------------------------------------------
  * Serving: a persistent request loop on one GPU with continuous batching
  * (paper Sect. 2, Fig. 1: several host processes sharing one GPU).

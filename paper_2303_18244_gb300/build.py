@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 
-HAND = ["mg_runtime.cu", "mg_server.cu", "mg_diag.cu"]
+HAND = ["mg_runtime.cu", "mg_server.cu", "mg_diag.cu", "mg_static.cu"]
 
 
 def _write_if_changed(path: str, text: str) -> None:

@@ -27,6 +27,7 @@ MG_PHOTON_ONLY = 2
 EXPORTS = (
     "mg_params_default", "mg_process_create", "mg_process_destroy", "mg_process_info",
     "mg_good_helicities", "mg_sigma", "mg_sigma_host", "mg_process_status", "mg_sigma_helicities",
+    "mg_good_helicities_static",
     "mg_server_cfg_default", "mg_server_create", "mg_server_submit", "mg_server_poll",
     "mg_server_destroy", "mg_strerror",
     # include/mg_diag.h
@@ -76,6 +77,7 @@ def lib() -> ctypes.CDLL:
         ip = ctypes.POINTER(ctypes.c_int)
         L.mg_process_info.argtypes = [vp, ip, ip, ip, ip, dp]
         L.mg_good_helicities.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
+        L.mg_good_helicities_static.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
         L.mg_sigma.argtypes = [vp, vp, i64, vp, vp]
         L.mg_sigma_host.argtypes = [vp, vp, i64, vp, vp]
         L.mg_process_status.argtypes = [vp]
@@ -181,6 +183,19 @@ def good_helicities(h: Process, momenta_dev, nevt: int | None = None):
     mask = np.zeros(h.info.n_hel, dtype=np.uint8)
     _check(lib().mg_good_helicities(h.handle, ptr, nevt, ctypes.byref(n),
                                     mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))), "mg_good_helicities")
+    return n.value, mask
+
+
+def good_helicities_static(h: Process, momenta_dev, nevt: int | None = None):
+    """(n_good, mask) -- mg_good_helicities_static: the helicity filter for
+    callers that cannot allocate device memory (scratch in a fixed device array)."""
+    nevt = momenta_dev.shape[0] if nevt is None else nevt
+    ptr = _dev_check(momenta_dev) if nevt else None
+    n = ctypes.c_int()
+    mask = np.zeros(h.info.n_hel, dtype=np.uint8)
+    _check(lib().mg_good_helicities_static(h.handle, ptr, nevt, ctypes.byref(n),
+                                           mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+           "mg_good_helicities_static")
     return n.value, mask
 
 
