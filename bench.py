@@ -38,6 +38,13 @@ PROC = "g g > t t~ g g"
 SQRTS = 1500.0
 SEED = 3
 NEVT = 524288
+# the other configurations of the workload set (--proc): process, sqrt(s), seed, events
+WORKLOADS = {
+    "eemumu": ("e+ e- > mu+ mu-", 500.0, 1, 16384),
+    "ggtt": ("g g > t t~", 1000.0, 2, 524288),
+    "ggttgg": ("g g > t t~ g g", 1500.0, 3, 524288),
+    "ggttggg": ("g g > t t~ g g g", 2000.0, 4, 65536),
+}
 METRIC = "gg→tt̄gg MEs/s on 1 GB300, FP64 vs mixed (≤1e-5 rel err); serve p50/p99 ms"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -168,12 +175,19 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--nevt", type=int, default=NEVT)
+    ap.add_argument("--proc", default="ggttgg", choices=sorted(WORKLOADS))
+    ap.add_argument("--nevt", type=int, default=None)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--serve", action="store_true", help="also run the serving benchmark")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve", action="store_true",
+                    help="full serving benchmark (400 requests, mixed and FP64) instead of the short mixed one")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    global PROC, SQRTS, SEED, NEVT
+    PROC, SQRTS, SEED, NEVT = WORKLOADS[args.proc]
+    if args.nevt is None:
+        args.nevt = NEVT
     if args.impl == "reference":
         return run_reference(args)
 
@@ -252,7 +266,7 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_t = max_over_ranks([statistics.median(e2e_ms)], device="cuda")[0]
 
-    fl = load_flops("ggttgg")
+    fl = load_flops(args.proc)
     flops_evt = ngood * (fl["amp_flops_per_hel"] + fl["colour_dense_flops_per_hel"])
     kernel_ms = t_mix / args.steps
     achieved = flops_evt * nevt / (kernel_ms * 1e-3) / 1e12
@@ -277,7 +291,7 @@ def main():
                 "h2d_bytes_per_step": int(p.nbytes), "d2h_bytes_per_step": int(nevt * 8)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                      "frac": achieved / peak32, "traffic": None,
-                     "kernel": "sigma_kernel<ggttgg, float>",
+                     "kernel": f"sigma kernel of {args.proc}, mixed",
                      "flops_per_event": flops_evt,
                      "peak_source": "measured FP32 FMA loop (mg_diag), burst"},
         "gpu_launches": args.steps,
@@ -287,8 +301,10 @@ def main():
         v, cores, n, dt = time_oracle(PROC, SQRTS, SEED, first)
         res["cpu_baseline"] = {"value": v, "unit": "MEs/s", "cores": cores, "kind": "oracle",
                                "sample": f"{n} events of the workload ({dt:.1f} s wall)"}
-    if args.serve:
-        res["serve"] = serve_bench(args, mg, process_momenta)
+    if not args.no_serve and args.proc == "ggttgg":
+        nreq = args.serve_requests or (400 if args.serve else 120)
+        precs = ("mixed", "fp64") if args.serve else ("mixed",)
+        res["serve"] = serve_bench(nreq, precs, mg, process_momenta)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
@@ -296,21 +312,23 @@ def main():
     return 0
 
 
-def serve_bench(args, mg, process_momenta):
+def serve_bench(nreq, precs, mg, process_momenta):
     """Poisson arrivals (mean gap 2 ms) of requests drawn uniformly from four
     processes, log-uniform 256..65536 events each (Philox seed 5 drives the
     choices), served by the continuous-batching loop; p50/p99 latency."""
     from paper_2303_18244_gb300.inputs import uniforms
     out = {}
     for prec_name, prec in (("mixed", mg.MG_MIXED), ("fp64", mg.MG_FP64)):
+        if prec_name not in precs:
+            continue
         handles = {p: mg.Process(p, precision=prec) for p in SERVE_PROCS}
         for p, hh in handles.items():
             calib = process_momenta(p, SERVE_PROCS[p], 1024, 1005)
             import torch
             mg.good_helicities(hh, torch.from_numpy(calib).cuda())
-        u = uniforms(5, 0, args.serve_requests, 1)[:, 0, :]
+        u = uniforms(5, 0, nreq, 1)[:, 0, :]
         reqs = []
-        for i in range(args.serve_requests):
+        for i in range(nreq):
             proc = list(SERVE_PROCS)[min(3, int(u[i, 0] * 4))]
             n = int(round(math.exp(math.log(256) + u[i, 1] * (math.log(65536) - math.log(256)))))
             gap = -2e-3 * math.log(u[i, 2])
@@ -337,7 +355,9 @@ def serve_bench(args, mg, process_momenta):
         wall = time.perf_counter() - t0
         srv.close()
         out[prec_name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                          "MEs_per_s": tot / wall, "requests": len(reqs), "events": tot}
+                          "MEs_per_s": tot / wall, "requests": len(reqs), "events": tot,
+                          "workload": "Poisson arrivals (mean 2 ms), processes uniform over "
+                                      "ee->mumu/gg->tt~/gg->tt~gg/gg->tt~ggg, log-uniform 256-65536 events, seed 5"}
     return out
 
 

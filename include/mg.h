@@ -151,6 +151,19 @@ int mg_sigma_helicities(mg_process* h, const double* momenta_dev, int64_t nevt, 
 int mg_good_helicities_static(mg_process* h, const double* momenta_dev, int64_t nevt, int* n_good_out,
                               uint8_t* mask_host);
 
+/* Flat phase-space momenta generated on the device (paper Sect. 2: the
+ * random-number -> momenta step of the event generator, moved to the GPU):
+ * momenta_dev[nevt][npar][4] for events first_event .. first_event+nevt-1 of
+ * the stream (seed), at fixed sqrt_s [GeV], for the handle's process (top
+ * masses from its parameters).  Philox4x64-10 uniforms, key (seed, 0),
+ * counter (event, final-state slot, 0, 0), u = ((w >> 11) + 0.5) 2^-53; RAMBO
+ * massless generation, conformal map, residual 3-momentum removed, common
+ * 3-momentum scale onto the mass shells; initial states (E,0,0,+-E).  The same
+ * stream as the host input module to rounding of log/sin/cos.  Stream-ordered.
+ * Errors: MG_ERR_ARG (nevt < 0, first_event < 0, sqrt_s below threshold, NULL). */
+int mg_rambo(const mg_process* h, double sqrt_s, uint64_t seed, int64_t first_event, int64_t nevt,
+             double* momenta_dev, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: a persistent request loop on one GPU with continuous batching
  * (paper Sect. 2, Fig. 1: several host processes sharing one GPU).

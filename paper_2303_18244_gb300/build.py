@@ -22,7 +22,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
 
-HAND = ["mg_runtime.cu", "mg_server.cu", "mg_diag.cu", "mg_static.cu"]
+# extra nvcc flags (e.g. -DMG_TC_MINB=3 for a launch-shape sweep)
+FLAGS += os.environ.get("MG_NVCC_EXTRA", "").split()
+
+HAND = ["mg_runtime.cu", "mg_server.cu", "mg_diag.cu", "mg_static.cu", "mg_phasespace.cu"]
 
 
 def _write_if_changed(path: str, text: str) -> None:

@@ -123,9 +123,16 @@ struct LayoutTC {
   static constexpr uint32_t tmem_cols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
 };
 
+// CTAs per SM the register allocation is sized for (launch bounds).  At 2 the
+// straight-line gg -> t t~ g g code keeps 255 registers; 3 caps them at 168 and
+// its spills halve the throughput (measured).
+#ifndef MG_TC_MINB
+#define MG_TC_MINB 1
+#endif
+
 // Mixed-precision |M|^2 with the tensor-core colour sum; NT = 128 events per CTA.
 template <class P, int NT>
-__global__ void __launch_bounds__(NT) sigma_tc_kernel(const double* __restrict__ mom, long long nevt,
+__global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* __restrict__ mom, long long nevt,
                                                       double* __restrict__ me, const int* __restrict__ hels,
                                                       int nhel, KParams kp, const uint4* __restrict__ ctile,
                                                       unsigned* __restrict__ status) {

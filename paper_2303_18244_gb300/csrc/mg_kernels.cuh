@@ -83,11 +83,18 @@ constexpr uint32_t WAIT_POLLS = 1u << 22;
 // Each thread reads and writes only its own column of the slab and of the
 // colour-flow accumulators, so the helicity loop needs no block barrier.
 // ---------------------------------------------------------------------------
+// slab slots kept per thread (the lean layout drops the external-state
+// ingredients, which the FP32 code then recomputes per helicity)
+template <class P, typename R>
+constexpr int slab_slots() {
+  return sizeof(R) == 4 ? (P::LEAN_SLAB ? P::NSLOT_LEAN : P::NSLOT_K) : P::NSLOT;
+}
+
 template <class P, typename R, int NT>
 struct Layout {
   static constexpr size_t bar_bytes = 128;
   static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
-  static constexpr size_t slab_bytes = size_t(NT) * P::NSLOT * sizeof(R);
+  static constexpr size_t slab_bytes = size_t(NT) * slab_slots<P, R>() * sizeof(R);
   static constexpr size_t jamp_bytes = size_t(NT) * P::NCOL * sizeof(cx<R>);
   static constexpr size_t slab_off = bar_bytes + ((stage_bytes + 127) / 128) * 128;
   static constexpr size_t jamp_off = slab_off + ((slab_bytes + 127) / 128) * 128;

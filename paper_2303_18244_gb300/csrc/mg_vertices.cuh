@@ -251,6 +251,56 @@ __device__ __forceinline__ void vector_basis(const double k[4], double out[6]) {
   out[5] = 0.0;
 }
 
+// Same ingredients in the compute precision R, from a momentum in R: used by
+// the FP32 path, which recomputes them per helicity instead of keeping them in
+// shared memory (a few flops against tens of thousands per helicity).
+template <typename R>
+__device__ __forceinline__ FermIngr<R> fermion_ingredients_r(const R p[4], R m) {
+  const R pt2 = p[1] * p[1] + p[2] * p[2];
+  const R P = sqrt(pt2 + p[3] * p[3]);
+  const R E = p[0];
+  FermIngr<R> f;
+  f.om_p = sqrt(E + P);
+  f.om_m = (m == R(0)) ? R(0) : sqrt(m * m / (E + P));
+  const R s = (p[3] >= R(0)) ? (P + p[3]) : (pt2 / (P - p[3]));
+  if (s > R(0)) {
+    f.a = sqrt(s / (R(2) * P));
+    const R r = R(1) / sqrt(R(2) * P * s);
+    f.bre = p[1] * r;
+    f.bim = p[2] * r;
+  } else {
+    f.a = R(0);
+    f.bre = R(1);
+    f.bim = R(0);
+  }
+  return f;
+}
+template <typename R>
+__device__ __forceinline__ void vector_basis_r(const R k[4], R e1[3], R e2[3]) {
+  const R pt2 = k[1] * k[1] + k[2] * k[2];
+  const R P = sqrt(pt2 + k[3] * k[3]);
+  R cph, sph, cth, sth;
+  if (pt2 > R(0)) {
+    const R pt = sqrt(pt2);
+    cph = k[1] / pt;
+    sph = k[2] / pt;
+    cth = k[3] / P;
+    sth = pt / P;
+  } else {
+    cph = R(1);
+    sph = R(0);
+    cth = (k[3] >= R(0)) ? R(1) : R(-1);
+    sth = R(0);
+  }
+  const R r = R(0.70710678118654752440);
+  e1[0] = r * cth * cph;
+  e1[1] = r * cth * sph;
+  e1[2] = -r * sth;
+  e2[0] = -r * sph;
+  e2[1] = r * cph;
+  e2[2] = R(0);
+}
+
 // ---------------------------------------------------------------------------
 // vertices
 // ---------------------------------------------------------------------------

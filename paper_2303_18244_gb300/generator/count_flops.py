@@ -29,8 +29,11 @@ PROGRAM = r"""
 #include <cmath>
 #include <cstdio>
 #define __device__
+#define __host__
 #define __forceinline__ inline
 #define __restrict__
+struct int4 { int x, y, z, w; };
+template <typename T> inline T __ldg(const T* p) { return *p; }
 static long long n_add = 0, n_mul = 0;
 struct Cnt {
   double v;
@@ -42,6 +45,7 @@ inline Cnt operator-(Cnt a, Cnt b) { n_add++; return Cnt(a.v - b.v); }
 inline Cnt operator*(Cnt a, Cnt b) { n_mul++; return Cnt(a.v * b.v); }
 inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
 inline bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
+inline Cnt operator+(Cnt a, double b) { return a + Cnt(b); }
 #include "mg_vertices.cuh"
 #include "gen/TAG.cuh"
 using namespace mg;
@@ -51,10 +55,10 @@ int main() {
   double kp[8] = {1.2, 173.0, 1.5, 0.5, 0.2, 0.3, 91.0, 2.4};
   cx<Cnt> jamp[TAG::NCOL];
   n_add = n_mul = 0;
-  TAG::amplitudes<Cnt>(ev, 1, 5, kp, jamp);
+  TAG::amplitudes<Cnt>(ev, 1, 5, kp, jamp, 1);
   long long amp = n_add + n_mul;
   n_add = n_mul = 0;
-  volatile double s = TAG::colour_quadratic<Cnt>(jamp).v;
+  volatile double s = TAG::colour_quadratic<Cnt>(jamp, 1).v;
   (void)s;
   long long col = n_add + n_mul;
   printf("%lld %lld %d %d\n", amp, col, TAG::NHEL, TAG::NCOL);

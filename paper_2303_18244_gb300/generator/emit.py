@@ -69,7 +69,7 @@ def _colour_quadratic(K, ncol) -> list[str]:
     return out
 
 
-def emit_gg(n: int, tag: str) -> str:
+def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     npar = n + 2
     nhel = 1 << npar
     plan = build_plan(n)
@@ -83,14 +83,14 @@ def emit_gg(n: int, tag: str) -> str:
     slots = [0, 1] + list(range(4, n + 2))  # gluon index -> particle slot
     full = (1 << n) - 1
 
+    # slab layout: momenta and propagator coefficients first (the "lean" part
+    # that the FP32 path keeps), then the FP64 external-state ingredients that
+    # only the FP64 path stores (FP32 recomputes them per helicity)
     S = _Slots()
     for i in range(n):
         S.alloc(f"k{i}", 4)
-        S.alloc(f"e{i}", 6)
     S.alloc("pt", 4)
-    S.alloc("ft", 5)
     S.alloc("ptb", 4)
-    S.alloc("ftb", 5)
     gmasks = sorted({op[-1] for op in plan.ops if op[0] in ("3", "4")})
     fmasks = set()
     for op in plan.ops:
@@ -104,7 +104,17 @@ def emit_gg(n: int, tag: str) -> str:
     for m in fmasks:
         S.alloc(f"cf{m}", 2)
     S.alloc("cgtt", 1)
+    nslot_lean = S.n
+    for i in range(n):
+        S.alloc(f"e{i}", 6)
+    S.alloc("ft", 5)
+    S.alloc("ftb", 5)
     nslot = S.n
+    # table mode, FP32 path: every gluon-subset momentum sum, precomputed per event
+    if mode == "table":
+        for m in range(1, full + 1):
+            S.alloc(f"K{m}", 4)
+    nslot_k = S.n
     sl = S.names
 
     L = []
@@ -119,6 +129,12 @@ def emit_gg(n: int, tag: str) -> str:
     L.append(f"static constexpr int NDIAG = {ndiag};")
     L.append(f"static constexpr int NAMP = {len(plan.amps)};")
     L.append(f"static constexpr int NSLOT = {nslot};")
+    L.append(f"static constexpr int NSLOT_K = {nslot_k};  // + precomputed subset momenta (table mode, FP32)")
+    L.append(f"static constexpr int KBASE = {sl['K1'] if mode == 'table' else 0};")
+    L.append(f"static constexpr int NSLOT_LEAN = {nslot_lean};  // slots without the external-state ingredients")
+    L.append("// FP32 path: recompute the external-state ingredients per helicity instead of")
+    L.append("// keeping them in shared memory (measured slower while registers bound occupancy)")
+    L.append("static constexpr bool LEAN_SLAB = false;")
     L.append(f"static constexpr double IDEN = {iden}.0;")
     L.append(f"static constexpr int CDEN = {cden};")
     L.append(f"static constexpr int KNUM[NCOL * NCOL] = {{{_fmt_knum(K)}}};")
@@ -134,17 +150,17 @@ def emit_gg(n: int, tag: str) -> str:
         s = slots[i]
         sign = "" if s < 2 else "-"
         L.append(f"  double k{i}[4] = {{{', '.join(f'{sign}p[{4 * s + mu}]' for mu in range(4))}}};")
-        L.append(f"  {{ double b[6]; vector_basis(p + {4 * s}, b);")
         for mu in range(4):
-            L.append(f"    EV({sl[f'k{i}'] + mu}) = R(k{i}[{mu}]);")
+            L.append(f"  EV({sl[f'k{i}'] + mu}) = R(k{i}[{mu}]);")
+        L.append(f"  {{ double b[6]; vector_basis(p + {4 * s}, b);")
         for j in range(6):
             L.append(f"    EV({sl[f'e{i}'] + j}) = R(b[{j}]);")
         L.append("  }")
     for name, s in (("pt", 2), ("ptb", 3)):
         fname = "ft" if name == "pt" else "ftb"
-        L.append(f"  {{ double f[5]; fermion_ingredients(p + {4 * s}, mt, f);")
         for mu in range(4):
-            L.append(f"    EV({sl[name] + mu}) = R(p[{4 * s + mu}]);")
+            L.append(f"  EV({sl[name] + mu}) = R(p[{4 * s + mu}]);")
+        L.append(f"  {{ double f[5]; fermion_ingredients(p + {4 * s}, mt, f);")
         for j in range(5):
             L.append(f"    EV({sl[fname] + j}) = R(f[{j}]);")
         L.append("  }")
@@ -170,9 +186,21 @@ def emit_gg(n: int, tag: str) -> str:
     L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
     L.append("    const double P2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];")
     L.append(f"    EV({sl['cgtt']}) = R(g / P2); }}")
+    if mode == "table":
+        L.append("  if constexpr (sizeof(R) == 4) {")
+        for m in range(1, full + 1):
+            comps = ksum_fp64(m)
+            for mu in range(4):
+                L.append(f"    EV({sl[f'K{m}'] + mu}) = R({comps[mu]});")
+        L.append("  }")
     L.append("#undef EV")
     L.append("}")
     L.append("")
+    if mode == "table":
+        L.extend(_table_sections(plan, tag, n, npar, ncol, sl, slots, full, K))
+        L.append(f"}};  // struct {tag}")
+        L.append("}  // namespace mg")
+        return "\n".join(L) + "\n"
     # ---------------- amplitudes ----------------
     L.append("// one helicity: currents and amplitudes, diagram by diagram, into the colour flows")
     L.append("template <typename R>")
@@ -211,21 +239,11 @@ def emit_gg(n: int, tag: str) -> str:
         name = f"w{cid}"
         if kind == "ext":
             i = op[1]
-            s = slots[i]
-            e = sl[f"e{i}"]
-            out = "true" if s >= 2 else "false"
-            L.append(f"  V4<R> {name};")
-            L.append(f"  {{ const R e1[3] = {{EV({e}), EV({e + 1}), EV({e + 2})}}; "
-                     f"const R e2[3] = {{EV({e + 3}), EV({e + 4}), EV({e + 5})}};")
-            L.append(f"    {name} = ext_vector<R>(e1, e2, R(l{s}), {out}); }}")
+            L.extend(_ext_gluon_lines(name, i, slots[i], sl, declare=True))
         elif kind == "ubar":
-            f = sl["ft"]
-            L.append(f"  const Sp<R> {name} = ext_ubar<R>(FermIngr<R>{{EV({f}), EV({f + 1}), EV({f + 2}), "
-                     f"EV({f + 3}), EV({f + 4})}}, l2);")
+            L.extend(_ext_top_lines(name, "ubar", sl, declare=True))
         elif kind == "v":
-            f = sl["ftb"]
-            L.append(f"  const Sp<R> {name} = ext_v<R>(FermIngr<R>{{EV({f}), EV({f + 1}), EV({f + 2}), "
-                     f"EV({f + 3}), EV({f + 4})}}, l3);")
+            L.extend(_ext_top_lines(name, "v", sl, declare=True))
         elif kind == "gtt":
             a = cur(plan.keys[("row", ())])
             b = cur(plan.keys[("col", ())])
@@ -408,6 +426,214 @@ def schedule(plan) -> list[int]:
     return order
 
 
+def _ext_gluon_lines(name, i, pslot, sl, declare):
+    """External gluon i (particle slot pslot): polarisation basis from the slab
+    (FP64 path) or recomputed from the stored momentum (FP32 path)."""
+    e = sl[f"e{i}"]
+    k = sl[f"k{i}"]
+    out = "true" if pslot >= 2 else "false"
+    sign = "-" if pslot >= 2 else ""  # physical momentum = +-(incoming momentum)
+    L = [f"  V4<R> {name};"] if declare else []
+    L.append("  {")
+    L.append("    R e1[3], e2[3];")
+    L.append("    if constexpr (LEAN_SLAB && sizeof(R) == 4) {")
+    L.append(f"      const R pk[4] = {{{sign}EV({k}), {sign}EV({k + 1}), {sign}EV({k + 2}), {sign}EV({k + 3})}};")
+    L.append("      vector_basis_r<R>(pk, e1, e2);")
+    L.append("    } else {")
+    L.append(f"      e1[0] = EV({e}); e1[1] = EV({e + 1}); e1[2] = EV({e + 2});")
+    L.append(f"      e2[0] = EV({e + 3}); e2[1] = EV({e + 4}); e2[2] = EV({e + 5});")
+    L.append("    }")
+    L.append(f"    {name} = ext_vector<R>(e1, e2, R(l{pslot}), {out});")
+    L.append("  }")
+    return L
+
+
+def _ext_top_lines(name, kind, sl, declare, wrap=False):
+    """Outgoing top (ubar) or antitop (v): spinor ingredients from the slab
+    (FP64 path) or recomputed from the stored momentum (FP32 path)."""
+    f = sl["ft" if kind == "ubar" else "ftb"]
+    pm = sl["pt" if kind == "ubar" else "ptb"]
+    lam = "l2" if kind == "ubar" else "l3"
+    fn = "ext_ubar" if kind == "ubar" else "ext_v"
+    typ = "Sp<R>"
+    L = [f"  {typ} {name};"] if declare else []
+    L.append("  {")
+    L.append("    FermIngr<R> fi;")
+    L.append("    if constexpr (LEAN_SLAB && sizeof(R) == 4) {")
+    L.append(f"      const R pp[4] = {{EV({pm}), EV({pm + 1}), EV({pm + 2}), EV({pm + 3})}};")
+    L.append("      fi = fermion_ingredients_r<R>(pp, R(kp[1]));")
+    L.append("    } else {")
+    L.append(f"      fi = FermIngr<R>{{EV({f}), EV({f + 1}), EV({f + 2}), EV({f + 3}), EV({f + 4})}};")
+    L.append("    }")
+    rhs = f"{fn}<R>(fi, {lam})"
+    L.append(f"    {name} = {'as_v4(' + rhs + ')' if wrap else rhs};")
+    L.append("  }")
+    return L
+
+
+def program(plan) -> list[tuple[str, int]]:
+    """Linear evaluation order: ("cur", id) on first use, ("amp", index) --
+    the order in which the straight-line emitter writes the code."""
+    seq = []
+    done = set()
+    gtt = plan.keys.get(("gtt",))
+
+    def cur(c):
+        if c in done:
+            return
+        op = plan.ops[c]
+        k = op[0]
+        if k == "gtt":
+            cur(plan.keys[("row", ())])
+            cur(plan.keys[("col", ())])
+        elif k == "3":
+            cur(op[1]); cur(op[2])
+        elif k == "4":
+            cur(op[1]); cur(op[2]); cur(op[3])
+        elif k == "row":
+            cur(op[1]); cur(op[2])
+        elif k == "col":
+            cur(op[1]); cur(op[2])
+        done.add(c)
+        seq.append(("cur", c))
+
+    for ai in schedule(plan):
+        op = plan.amps[ai][0]
+        if op[0] == "f":
+            cur(op[1]); cur(op[2]); cur(op[3])
+        elif op[0] == "a3":
+            cur(gtt); cur(op[1]); cur(op[2])
+        else:
+            cur(gtt); cur(op[1]); cur(op[2]); cur(op[3])
+        seq.append(("amp", ai))
+    return seq
+
+
+def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
+    """Op table + interpreter-driven amplitudes() and a looped colour form."""
+    seq = program(plan)
+    gtt = plan.keys.get(("gtt",))
+    # inputs of every step, for liveness
+    def inputs(kind, i):
+        if kind == "cur":
+            return current_deps(plan, i)
+        return amp_deps(plan, plan.amps[i][0])
+    last = {}
+    for t, (kind, i) in enumerate(seq):
+        for d in inputs(kind, i):
+            last[d] = t
+    slot = {}
+    free = []
+    nstore = 0
+    ops = []
+    jl = []
+    ext_kinds = ("ext", "ubar", "v")
+    for t, (kind, i) in enumerate(seq):
+        if kind == "cur":
+            if free:
+                free.sort()
+                slot[i] = free.pop(0)
+            else:
+                slot[i] = nstore
+                nstore += 1
+            op = plan.ops[i]
+            k = op[0]
+            out = slot[i]
+            if k == "3":
+                ops.append([1, out, slot[op[1]], slot[op[2]], _mask_of(plan, op[1]), _mask_of(plan, op[2]),
+                            sl[f"cg{op[3]}"], 0])
+            elif k == "4":
+                ops.append([2, out, slot[op[1]], slot[op[2]], slot[op[3]], op[4], sl[f"cg{op[5]}"], 0])
+            elif k == "row":
+                ops.append([3, out, slot[op[1]], slot[op[2]], op[3], sl[f"cf{op[3]}"], 0, 0])
+            elif k == "col":
+                ops.append([4, out, slot[op[1]], slot[op[2]], op[3], sl[f"cf{full ^ op[3]}"], 0, 0])
+            elif k == "gtt":
+                ops.append([5, out, slot[plan.keys[("row", ())]], slot[plan.keys[("col", ())]], sl["cgtt"],
+                            0, 0, 0])
+            else:
+                assert k in ext_kinds
+        else:
+            op, co = plan.amps[i]
+            j0 = len(jl)
+            for f, c in sorted(co.items()):
+                assert c in (1, -1), c
+                jl.append((f << 1) | (1 if c < 0 else 0))
+            nj = len(jl) - j0
+            if op[0] == "f":
+                ops.append([6, slot[op[1]], slot[op[2]], slot[op[3]], 0, 0, j0, nj])
+            elif op[0] == "a3":
+                ops.append([7, slot[op[1]], slot[op[2]], _mask_of(plan, op[1]), _mask_of(plan, op[2]), slot[gtt],
+                            j0, nj])
+            else:
+                ops.append([8, slot[op[1]], slot[op[2]], slot[op[3]], op[4], slot[gtt], j0, nj])
+        for d in inputs(kind, i):
+            if last[d] == t and plan.ops[d][0] not in ext_kinds:
+                free.append(slot[d])
+    L = []
+    L.append(f"static constexpr int NG = {n};")
+    chain = " : ".join(f"i == {i} ? {sl[f'k{i}']}" for i in range(n - 1)) + f" : {sl[f'k{n - 1}']}"
+    L.append("// slab offset of gluon i's incoming momentum")
+    L.append(f"__host__ __device__ static constexpr int koff(int i) {{ return {chain}; }}")
+    L.append(f"static constexpr int PT = {sl['pt']};")
+    L.append(f"static constexpr int PTB = {sl['ptb']};")
+    L.append(f"static constexpr int NOPS = {len(ops)};")
+    L.append(f"static constexpr int NSTORE = {nstore};")
+    L.append(f"static constexpr int NJL = {len(jl)};")
+    L.append("// per-helicity program: externals into the store, then the op table")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
+    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp,")
+    L.append("                                           const int js) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("  const R g = R(kp[0]);")
+    L.append("  const R mt = R(kp[1]);")
+    for i in range(npar):
+        L.append(f"  const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
+    L.append(f"  V4<R> W[{nstore}];")
+    gl_slots = [0, 1] + list(range(4, n + 2))
+    for i in range(n):
+        cid = plan.keys[("g", ("L", i))]
+        L.extend(_ext_gluon_lines(f"W[{slot[cid]}]", i, gl_slots[i], sl, declare=False))
+    L.extend(_ext_top_lines(f"W[{slot[plan.keys[('row', ())]]}]", "ubar", sl, declare=False, wrap=True))
+    L.extend(_ext_top_lines(f"W[{slot[plan.keys[('col', ())]]}]", "v", sl, declare=False, wrap=True))
+    L.append(f"  for (int c = 0; c < {ncol}; c++) jamp[c * js] = cx<R>{{R(0), R(0)}};")
+    L.append(f"  run_program<{tag}, R>({tag}_OPS, NOPS, {tag}_JL, ev, es, g, mt, W, jamp, js);")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("// sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j), KNUM from the table knum")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
+    L.append(f"  const short* __restrict__ knum = {tag}_KNUM;")
+    L.append("  R acc = R(0);")
+    L.append("#pragma unroll 1")
+    L.append(f"  for (int i = 0; i < {ncol}; i++) {{")
+    L.append("    R yr = R(0), yi = R(0);")
+    L.append(f"    for (int j = 0; j < {ncol}; j++) {{")
+    L.append(f"      const R k = R(__ldg(knum + i * {ncol} + j));")
+    L.append("      yr = fmaf_t<R>(k, jamp[j * js].re, yr);")
+    L.append("      yi = fmaf_t<R>(k, jamp[j * js].im, yi);")
+    L.append("    }")
+    L.append("    acc = fmaf_t<R>(jamp[i * js].re, yr, acc);")
+    L.append("    acc = fmaf_t<R>(jamp[i * js].im, yi, acc);")
+    L.append("  }")
+    L.append("  return acc;")
+    L.append("}")
+    # data tables (outside the struct: emitted after it by the caller)
+    table_src = []
+    table_src.append(f"static __device__ const int4 {tag}_OPS[{2 * len(ops)}] = {{")
+    for o in ops:
+        table_src.append(f"  {{{o[0]}, {o[1]}, {o[2]}, {o[3]}}}, {{{o[4]}, {o[5]}, {o[6]}, {o[7]}}},")
+    table_src.append("};")
+    table_src.append(f"static __device__ const short {tag}_JL[{len(jl)}] = {{{', '.join(map(str, jl))}}};")
+    table_src.append(f"static __device__ const short {tag}_KNUM[{ncol * ncol}] = {{{_fmt_knum(K)}}};")
+    _TABLES[tag] = table_src
+    return L
+
+
+_TABLES: dict = {}
+
+
 def _mask_of(plan, cid) -> int:
     op = plan.ops[cid]
     if op[0] == "ext":
@@ -434,6 +660,10 @@ def emit_eemumu(tag: str) -> str:
     L.append("static constexpr int NDIAG = 2;")
     L.append("static constexpr int NAMP = 2;")
     L.append("static constexpr int NSLOT = 23;")
+    L.append("static constexpr int NSLOT_K = 23;")
+    L.append("static constexpr int KBASE = 0;")
+    L.append("static constexpr int NSLOT_LEAN = 23;")
+    L.append("static constexpr bool LEAN_SLAB = false;")
     L.append("static constexpr double IDEN = 4.0;")
     L.append("static constexpr int CDEN = 1;")
     L.append("static constexpr int KNUM[1] = {1};")
@@ -486,11 +716,20 @@ def emit_eemumu(tag: str) -> str:
     return "\n".join(L) + "\n"
 
 
+# processes evaluated by the table interpreter (straight-line code too large to compile)
+TABLE_MODE = {"ggttggg"}
+
+
 def emit(proc: str) -> tuple[str, str]:
     """(tag, header source) for a process string."""
     tag, n = PROCESSES[proc]
     if n == 0:
         return tag, emit_eemumu(tag)
+    if tag in TABLE_MODE:
+        src = emit_gg(n, tag, mode="table")
+        tables = "\n".join(_TABLES.pop(tag))
+        src = src.replace('#include "mg_vertices.cuh"', '#include "mg_vertices.cuh"\n#include "mg_interp.cuh"')
+        return tag, src.replace(f"struct {tag} {{", f"{tables}\nstruct {tag} {{", 1)
     return tag, emit_gg(n, tag)
 
 
@@ -500,7 +739,7 @@ THREADS = {
     "ggtt": (128, 128),
     "ggttg": (128, 128),
     "ggttgg": (64, 128),
-    "ggttggg": (64, 128),
+    "ggttggg": (64, 64),
 }
 
 

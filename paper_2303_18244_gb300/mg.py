@@ -27,7 +27,7 @@ MG_PHOTON_ONLY = 2
 EXPORTS = (
     "mg_params_default", "mg_process_create", "mg_process_destroy", "mg_process_info",
     "mg_good_helicities", "mg_sigma", "mg_sigma_host", "mg_process_status", "mg_sigma_helicities",
-    "mg_good_helicities_static",
+    "mg_good_helicities_static", "mg_rambo",
     "mg_server_cfg_default", "mg_server_create", "mg_server_submit", "mg_server_poll",
     "mg_server_destroy", "mg_strerror",
     # include/mg_diag.h
@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
         L.mg_good_helicities.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
         L.mg_good_helicities_static.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
         L.mg_sigma.argtypes = [vp, vp, i64, vp, vp]
+        L.mg_rambo.argtypes = [vp, ctypes.c_double, ctypes.c_uint64, i64, i64, vp, vp]
         L.mg_sigma_host.argtypes = [vp, vp, i64, vp, vp]
         L.mg_process_status.argtypes = [vp]
         L.mg_sigma_helicities.argtypes = [vp, vp, i64, vp, vp]
@@ -204,6 +205,13 @@ def sigma(h: Process, momenta_dev, me_out_dev, stream=None, nevt: int | None = N
     nevt = momenta_dev.shape[0] if nevt is None else nevt
     _check(lib().mg_sigma(h.handle, _dev_check(momenta_dev), nevt, _dev_check(me_out_dev), _stream_ptr(stream)),
            "mg_sigma")
+
+
+def rambo(h: Process, sqrt_s: float, seed: int, first_event: int, momenta_dev, stream=None):
+    """mg_rambo: fill momenta_dev[nevt][npar][4] with device-generated phase space."""
+    nevt = momenta_dev.shape[0]
+    _check(lib().mg_rambo(h.handle, sqrt_s, seed, first_event, nevt, _dev_check(momenta_dev),
+                          _stream_ptr(stream)), "mg_rambo")
 
 
 def sigma_helicities(h: Process, momenta_dev, out_dev, stream=None):
