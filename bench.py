@@ -243,8 +243,14 @@ def main():
     assert mg.process_status(hmix) == 0
     ms_64 = timed(h64, out64, args.fp64_steps, 1)
     assert mg.process_status(h64) == 0
+    # the paper's own mixed mode (FP64 diagrams, FP32 colour algebra) for comparison
+    hpap = mg.Process(PROC, precision=mg.MG_MIXED_PAPER)
+    mg.good_helicities(hpap, torch.from_numpy(calib).cuda())
+    outp = torch.empty(nevt, dtype=torch.float64, device="cuda")
+    ms_pap = timed(hpap, outp, 1, 1)
+    assert mg.process_status(hpap) == 0
 
-    t_mix, t_64 = max_over_ranks([sum(ms_mix), sum(ms_64) / len(ms_64)], device="cuda")
+    t_mix, t_64, t_pap = max_over_ranks([sum(ms_mix), sum(ms_64) / len(ms_64), sum(ms_pap)], device="cuda")
     value = world * nevt * args.steps / (t_mix * 1e-3)
     value64 = world * nevt / (t_64 * 1e-3)
 
@@ -285,6 +291,8 @@ def main():
         "fp64": {"value": value64, "unit": "MEs/s", "ms_per_step": t_64,
                  "roofline": {"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
                               "frac": achieved64 / peak64, "peak_source": "measured FP64 FMA loop (mg_diag)"}},
+        "paper_mixed": {"value": world * nevt / (t_pap * 1e-3), "unit": "MEs/s",
+                        "what": "FP64 diagrams + FP32 colour algebra (the paper's mixed mode)"},
         "accuracy_mixed_vs_fp64": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
                                    "max": float(rel.max()), "events": nevt},
         "e2e": {"value": world * nevt / (e2e_t * 1e-3), "unit": "MEs/s",

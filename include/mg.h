@@ -58,6 +58,8 @@ extern "C" {
 #define MG_MIXED 1  /* FP32 wavefunctions/amplitudes, FP64 propagator denominators,
                        FP16 hi+lo colour contraction on the tensor cores with FP32
                        accumulation, FP64 helicity sum                            */
+#define MG_MIXED_PAPER 2 /* the paper's "mixed" (Sect. 3): Feynman diagrams in FP64,
+                       colour algebra in FP32 on CUDA cores, FP64 helicity sum    */
 
 /* flags */
 #define MG_NO_TOP_WIDTH 1   /* Gamma_t = 0 in every top propagator                 */
@@ -71,7 +73,7 @@ typedef struct {
   double wz;           /* Z width [GeV]                        default 2.441404  */
   double alpha_em_inv; /* 1/alpha_em                           default 132.507   */
   double gf;           /* Fermi constant [GeV^-2]              default 1.16639e-5 */
-  int precision;       /* MG_FP64 or MG_MIXED                                   */
+  int precision;       /* MG_FP64, MG_MIXED or MG_MIXED_PAPER                   */
   int flags;           /* MG_NO_TOP_WIDTH | MG_PHOTON_ONLY                      */
 } mg_params;
 
@@ -118,6 +120,21 @@ int mg_sigma_host(mg_process* h, const double* momenta_host, int64_t nevt, doubl
  * completed, otherwise MG_ERR_TIMEOUT (the kernel skipped its work and left the
  * outputs unwritten).  Synchronises the device.  Clears the word. */
 int mg_process_status(mg_process* h);
+
+/* ME per event plus the event-by-event random choice of a helicity and of a
+ * leading colour flow, as needed to write unweighted events (paper Sect. 5).
+ * rnd_dev[nevt][2] holds uniforms (r_hel, r_col) in [0, 1):
+ *   hel_out_dev[i]: the good helicity h_j (good list in increasing index
+ *     order) with the smallest j whose cumulative |M_h|^2 exceeds r_hel * ME;
+ *   col_out_dev[i]: the colour flow k (orderings of the gluons, lexicographic;
+ *     flow k is (T^{a_s1} ... T^{a_sn}) with s1 next to the top) with the
+ *     smallest k whose cumulative weight exceeds r_col * sum_k w_k, where
+ *     w_k = sum over good helicities of |J_k(h)|^2;
+ *   colw_out_dev (may be NULL): w[nevt][n_col].
+ * me_out_dev as mg_sigma (FP64, or mixed with the colour sum on CUDA cores).
+ * Stream-ordered.  Errors: MG_ERR_ARG, MG_ERR_CUDA. */
+int mg_sigma_select(mg_process* h, const double* momenta_dev, int64_t nevt, const double* rnd_dev,
+                    double* me_out_dev, int* hel_out_dev, int* col_out_dev, double* colw_out_dev, void* stream);
 
 /* Per-helicity |M_h|^2 / IDEN in FP64 for every helicity (not filtered):
  * out_dev[nevt][n_hel].  Stream-ordered.  Diagnostics and helicity selection. */

@@ -86,6 +86,7 @@ def _declare(L):
     L.mgo_polarisation.argtypes = [_D, ctypes.c_int, _D]
     L.mgo_gamma.argtypes = [_D]
     L.mgo_npar.argtypes = [ctypes.c_int]
+    L.mgo_flow_weights.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int64, _D]
     return L
 
 
@@ -103,19 +104,7 @@ def lib():
     global _lib
     with _lib_lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            L.mgo_me.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int64, _D]
-            for name in ("mgo_ordered_amps", "mgo_ordered_colour_sum", "mgo_dressed_colour_sum"):
-                getattr(L, name).argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _D]
-            L.mgo_colour_matrix.argtypes = [ctypes.c_int, _D]
-            L.mgo_permutations.argtypes = [ctypes.c_int, _I]
-            L.mgo_generators.argtypes = [_D]
-            L.mgo_fabc.argtypes = [_D]
-            L.mgo_spinor.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_int, _D]
-            L.mgo_polarisation.argtypes = [_D, ctypes.c_int, _D]
-            L.mgo_gamma.argtypes = [_D]
-            L.mgo_npar.argtypes = [ctypes.c_int]
-            _lib = L
+            _lib = _declare(ctypes.CDLL(build()))
     return _lib
 
 
@@ -158,6 +147,17 @@ def me(proc: str, momenta: np.ndarray, params: Params | None = None,
 
     with ThreadPoolExecutor(threads) as ex:
         list(ex.map(run, range(threads)))
+    return out
+
+
+def flow_weights(proc: str, momenta: np.ndarray, params: Params | None = None) -> np.ndarray:
+    """Per-event colour-flow weights sum_spins |A(sigma)|^2 (mgo_flow_weights)."""
+    import math
+    params = params or Params()
+    mom = np.ascontiguousarray(momenta, dtype=np.float64)
+    n = PROCS[proc] + 1
+    out = np.empty((mom.shape[0], math.factorial(n)), dtype=np.float64)
+    _check(lib().mgo_flow_weights(PROCS[proc], _p(params.array()), _p(mom), mom.shape[0], _p(out)))
     return out
 
 

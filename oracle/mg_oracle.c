@@ -842,8 +842,11 @@ static real me_eemumu(const oparams* o, const real* mom) {
   return sum / 4.0;
 }
 
-/* g(p1) g(p2) -> t(p3) t~(p4) g(p5) ... : n gluons in total */
-static real me_ggtt_ng(const oparams* o, int n, const real* mom) {
+/* g(p1) g(p2) -> t(p3) t~(p4) g(p5) ... : n gluons in total.
+ * flow_w (may be NULL): sum over spin states of |A(sigma)|^2 per ordering. */
+static real me_ggtt_ng_w(const oparams* o, int n, const real* mom, real* flow_w);
+static real me_ggtt_ng(const oparams* o, int n, const real* mom) { return me_ggtt_ng_w(o, n, mom, NULL); }
+static real me_ggtt_ng_w(const oparams* o, int n, const real* mom, real* flow_w) {
   const cplx* C = colour_matrix(n);
   if (!C) return NAN;
   const int np = factorial(n);
@@ -879,6 +882,8 @@ static real me_ggtt_ng(const oparams* o, int n, const real* mom) {
   real sum = 0.0;
   cplx A[MAXPERM];
   const int nhel = 1 << (n + 2);
+  if (flow_w)
+    for (int i = 0; i < np; i++) flow_w[i] = 0;
   for (int h = 0; h < nhel; h++) {
     for (int i = 0; i < n; i++)
       for (int mu = 0; mu < 4; mu++) q.eps[i][mu] = pol[i][(h >> i) & 1][mu]; /* real: eps* = eps */
@@ -892,6 +897,8 @@ static real me_ggtt_ng(const oparams* o, int n, const real* mom) {
     for (int i = 0; i < np; i++)
       for (int j = 0; j < np; j++) s += conj(A[i]) * C[i * np + j] * A[j];
     sum += creal(s);
+    if (flow_w)
+      for (int i = 0; i < np; i++) flow_w[i] += creal(A[i] * conj(A[i]));
   }
   real iden = 4.0 * 64.0;
   for (int i = 2; i <= n - 2; i++) iden *= i; /* identical final-state gluons */
@@ -912,6 +919,25 @@ int mgo_npar(int proc) {
   if (proc == MGO_EEMUMU) return 4;
   const int n = proc_gluons(proc);
   return n ? n + 2 : MGO_ERR_ARG;
+}
+
+/* Colour-flow weights w[i][sigma] = sum over spin states of |A(sigma)|^2
+ * (orderings lexicographic) for g g -> t t~ + gluons; the event-by-event
+ * choice of a leading colour flow draws sigma with probability w / sum w. */
+int mgo_flow_weights(int proc, const double* params, const double* mom, int64_t nevt, double* w) {
+  oparams o;
+  unpack_params(params, &o);
+  const int n = proc_gluons(proc);
+  if (!n || nevt < 0) return MGO_ERR_ARG;
+  if (!colour_matrix(n)) return MGO_ERR_NOMEM;
+  const int npar = n + 2, np = factorial(n);
+  for (int64_t e = 0; e < nevt; e++) {
+    real p[4 * (MAXG + 2)], fw[MAXPERM];
+    for (int i = 0; i < npar * 4; i++) p[i] = mom[(size_t)e * npar * 4 + i];
+    me_ggtt_ng_w(&o, n, p, fw);
+    for (int i = 0; i < np; i++) w[(size_t)e * np + i] = (double)fw[i];
+  }
+  return MGO_OK;
 }
 
 /* me[i] for events i in [0, nevt): mom = [nevt][npar][4] */

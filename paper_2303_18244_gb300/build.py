@@ -53,7 +53,7 @@ def processes() -> list[str]:
 def generate() -> list[str]:
     """Write csrc/gen/<tag>.cuh, <tag>_kernels.cu and registry.cu; return the TUs."""
     sys.path.insert(0, ROOT)
-    from paper_2303_18244_gb300.generator.emit import PROCESSES, emit, emit_kernels_tu
+    from paper_2303_18244_gb300.generator.emit import PROCESSES, emit, emit_kernels_tu, emit_select_tu
     os.makedirs(GEN, exist_ok=True)
     tus = []
     procs = processes()
@@ -71,6 +71,10 @@ def generate() -> list[str]:
         _write_if_changed(os.path.join(GEN, f"{tag}.cuh"), hdr)
         _, tu = emit_kernels_tu(proc)
         path = os.path.join(GEN, f"{tag}_kernels.cu")
+        _write_if_changed(path, tu)
+        tus.append(path)
+        _, tu = emit_select_tu(proc)
+        path = os.path.join(GEN, f"{tag}_select.cu")
         _write_if_changed(path, tu)
         tus.append(path)
     return tus
@@ -106,13 +110,15 @@ def build(verbose: bool = True) -> str:
     os.makedirs(BUILD, exist_ok=True)
     tus = generate() + [os.path.join(CSRC, f) for f in HAND]
     # largest units first so that they start early
-    tus.sort(key=lambda p: -os.path.getsize(p.replace("_kernels.cu", ".cuh")) if p.endswith("_kernels.cu") else 0)
-    # objects of processes not in this build must not be linked
-    stale = {os.path.join(BUILD, f) for f in os.listdir(BUILD) if f.endswith(".o")}
+    def weight(p):
+        for suf in ("_kernels.cu", "_select.cu"):
+            if p.endswith(suf):
+                return -os.path.getsize(p.replace(suf, ".cuh"))
+        return 0
+    tus.sort(key=weight)
     jobs = max(1, min(len(tus), os.cpu_count() or 1))
     with ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(_compile, tus))
-    del stale
+        objs = list(ex.map(_compile, tus))  # only this build's objects are linked
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -18,7 +18,11 @@
 //   OP_A3    a=f1 b=f2 maskA=f3 maskB=f4 gtt=f5 jl=f6 njl=f7   amplitude -g V3(a,b).G
 //   OP_A4    a=f1 b=f2 c=f3 br=f4 gtt=f5 jl=f6 njl=f7          amplitude +-g^2 L_br(a,b,c).G
 // cg, cf, cgtt: slab offsets of the per-event propagator coefficients
-// (cf: complex, two slots).  jl/njl index the colour list, whose entries are
+// (cf: complex, two slots).  Amplitudes come grouped by colour pattern (the
+// same flows with the same coefficients up to one overall sign): bit 8 of the
+// type word gives the amplitude's sign relative to its pattern (set: +1), the
+// amplitudes are summed in a register, and the last one of a group carries the
+// pattern's colour list jl/njl (njl = 0 on the others), whose entries are
 // (flow << 1) | (coefficient is -1).  P provides NG, koff(i) (slab offset of
 // gluon i's incoming momentum), PT and PTB (slab offsets of p_t and p_tbar).
 #pragma once
@@ -83,12 +87,17 @@ __device__ __forceinline__ void run_program(const int4* __restrict__ ops, int no
                                             const R* __restrict__ ev, int es, R g, R mt, V4<R>* W,
                                             cx<R>* __restrict__ jamp, int js) {
 #define EV(k) ev[(k) * es]
+  cx<R> pacc = {R(0), R(0)};  // running sum of the current colour pattern's amplitudes
 #pragma unroll 1
   for (int i = 0; i < nops; i++) {
     const int4 a = __ldg(ops + 2 * i);
     const int4 b = __ldg(ops + 2 * i + 1);
-    // a = (type, f1, f2, f3), b = (f4, f5, f6, f7)
-    switch (a.x) {
+    // a = (type | sign << 8, f1, f2, f3), b = (f4, f5, f6, f7)
+    const int type = a.x & 0xff;
+    const bool plus = (a.x >> 8) & 1;
+    cx<R> amp = {R(0), R(0)};
+    bool is_amp = false;
+    switch (type) {
       case OP_VVV: {
         R kx[4], ky[4];
         ksum<P, R>(ev, es, b.x, kx);
@@ -120,29 +129,33 @@ __device__ __forceinline__ void run_program(const int4* __restrict__ ops, int no
       case OP_GTT:
         W[a.y] = ffv_vcur<R>(as_sp(W[a.z]), as_sp(W[a.w]), cx<R>{R(0), EV(b.x)});
         break;
-      case OP_AF: {
-        const cx<R> amp = mul_i(g * ffv_amp<R>(as_sp(W[a.y]), W[a.z], as_sp(W[a.w])));
-        add_colour<R>(jl, b.z, b.w, amp, jamp, js);
+      case OP_AF:
+        amp = mul_i(g * ffv_amp<R>(as_sp(W[a.y]), W[a.z], as_sp(W[a.w])));
+        is_amp = true;
         break;
-      }
       case OP_A3: {
         R kx[4], ky[4];
         ksum<P, R>(ev, es, a.w, kx);
         ksum<P, R>(ev, es, b.x, ky);
-        const cx<R> amp = vvv_amp<R>(kx, W[a.y], ky, W[a.z], W[b.y], -g);
-        add_colour<R>(jl, b.z, b.w, amp, jamp, js);
+        amp = vvv_amp<R>(kx, W[a.y], ky, W[a.z], W[b.y], -g);
+        is_amp = true;
         break;
       }
-      case OP_A4: {
-        cx<R> amp;
+      case OP_A4:
         if (b.x == 0) amp = vvvv_amp<0, R>(W[a.y], W[a.z], W[a.w], W[b.y], g * g);
         else if (b.x == 1) amp = vvvv_amp<1, R>(W[a.y], W[a.z], W[a.w], W[b.y], g * g);
         else amp = vvvv_amp<2, R>(W[a.y], W[a.z], W[a.w], W[b.y], -g * g);
-        add_colour<R>(jl, b.z, b.w, amp, jamp, js);
+        is_amp = true;
         break;
-      }
       default:
         break;
+    }
+    if (is_amp) {
+      pacc = plus ? pacc + amp : pacc - amp;
+      if (b.w > 0) {
+        add_colour<R>(jl, b.z, b.w, pacc, jamp, js);
+        pacc = cx<R>{R(0), R(0)};
+      }
     }
   }
 #undef EV

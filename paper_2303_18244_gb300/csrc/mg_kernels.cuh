@@ -169,6 +169,111 @@ __global__ void __launch_bounds__(NT) sigma_kernel(const double* __restrict__ mo
   }
 }
 
+// |M|^2 plus the event-by-event random choice of a helicity and a leading
+// colour flow for unweighted events (paper Sect. 5: the last ingredient needed
+// by the event files).  rnd[e] = (r_hel, r_col) in [0, 1):
+//   helicity: the good helicity h_i with the smallest i whose cumulative
+//             |M_h|^2 (good list order) exceeds r_hel * sum;
+//   colour:   the flow k with the smallest k whose cumulative weight
+//             w_k = sum_h |J_k(h)|^2 exceeds r_col * sum_k w_k.
+// Colour sum on the CUDA cores in both precisions; optional per-flow weights.
+template <class P, typename R, int NT>
+__global__ void __launch_bounds__(NT)
+    select_kernel(const double* __restrict__ mom, long long nevt, const double* __restrict__ rnd,
+                  double* __restrict__ me, int* __restrict__ hel_out, int* __restrict__ col_out,
+                  double* __restrict__ colw_out, const int* __restrict__ hels, int nhel, KParams kp,
+                  unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using LY = Layout<P, R, NT>;
+  const int nvalid = load_and_prepare<P, R, NT>(smem, mom, nevt, kp, status);
+  if (nvalid < 0) return;
+  const R* ev = reinterpret_cast<const R*>(smem + LY::slab_off) + threadIdx.x;
+  cx<R>* jamp = reinterpret_cast<cx<R>*>(smem + LY::jamp_off) + threadIdx.x;
+  double mh[P::NHEL];
+  double w[P::NCOL];
+  for (int k = 0; k < P::NCOL; k++) w[k] = 0.0;
+  double acc = 0.0;
+#pragma unroll 1
+  for (int ih = 0; ih < nhel; ih++) {
+    const int h = __ldg(hels + ih);
+    P::template amplitudes<R>(ev, NT, h, kp.v, jamp, NT);
+    const double v = (double)P::template colour_quadratic<R>(jamp, NT);
+    mh[ih] = v;
+    acc += v;
+    for (int k = 0; k < P::NCOL; k++) {
+      const cx<R> j = jamp[k * NT];
+      w[k] += (double)j.re * (double)j.re + (double)j.im * (double)j.im;
+    }
+  }
+  if ((int)threadIdx.x >= nvalid) return;
+  const long long e = (long long)blockIdx.x * NT + threadIdx.x;
+  constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+  me[e] = acc * norm;
+  const double rh = rnd[2 * e], rc = rnd[2 * e + 1];
+  int sel = -1, last = 0;
+  double cum = 0.0;
+  const double th = rh * acc;
+  for (int ih = 0; ih < nhel; ih++) {
+    if (mh[ih] > 0.0) last = ih;
+    cum += mh[ih];
+    if (sel < 0 && cum > th && mh[ih] > 0.0) sel = ih;
+  }
+  hel_out[e] = __ldg(hels + (sel < 0 ? last : sel));
+  double wt = 0.0;
+  for (int k = 0; k < P::NCOL; k++) wt += w[k];
+  const double tc = rc * wt;
+  int ksel = -1, klast = 0;
+  cum = 0.0;
+  for (int k = 0; k < P::NCOL; k++) {
+    if (w[k] > 0.0) klast = k;
+    cum += w[k];
+    if (ksel < 0 && cum > tc && w[k] > 0.0) ksel = k;
+  }
+  col_out[e] = ksel < 0 ? klast : ksel;
+  if (colw_out)
+    for (int k = 0; k < P::NCOL; k++) colw_out[e * P::NCOL + k] = w[k];
+}
+
+// The paper's own "mixed" mode (Sect. 3): Feynman diagrams and colour flows
+// in FP64, the colour quadratic form in FP32 (colour numerators from a device
+// table knum[NCOL][NCOL], upper triangle doubled), helicity sum in FP64.
+template <class P, int NT>
+__global__ void __launch_bounds__(NT)
+    sigma_paper_kernel(const double* __restrict__ mom, long long nevt, double* __restrict__ me,
+                       const int* __restrict__ hels, int nhel, KParams kp, const short* __restrict__ knum,
+                       unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using LY = Layout<P, double, NT>;
+  const int nvalid = load_and_prepare<P, double, NT>(smem, mom, nevt, kp, status);
+  if (nvalid < 0) return;
+  const double* ev = reinterpret_cast<const double*>(smem + LY::slab_off) + threadIdx.x;
+  cx<double>* jamp = reinterpret_cast<cx<double>*>(smem + LY::jamp_off) + threadIdx.x;
+  double acc = 0.0;
+#pragma unroll 1
+  for (int ih = 0; ih < nhel; ih++) {
+    const int h = __ldg(hels + ih);
+    P::template amplitudes<double>(ev, NT, h, kp.v, jamp, NT);
+    float q = 0.f;
+#pragma unroll 1
+    for (int i = 0; i < P::NCOL; i++) {
+      const float jr = (float)jamp[i * NT].re, ji = (float)jamp[i * NT].im;
+      float yr = 0.f, yi = 0.f;
+      for (int j = i; j < P::NCOL; j++) {
+        const float k = (float)__ldg(knum + i * P::NCOL + j);
+        yr = fmaf(k, (float)jamp[j * NT].re, yr);
+        yi = fmaf(k, (float)jamp[j * NT].im, yi);
+      }
+      q = fmaf(jr, yr, q);
+      q = fmaf(ji, yi, q);
+    }
+    acc += (double)q;
+  }
+  if ((int)threadIdx.x < nvalid) {
+    constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+    me[(long long)blockIdx.x * NT + threadIdx.x] = acc * norm;
+  }
+}
+
 // Per-helicity |M_h|^2 / IDEN for every helicity, FP64 (helicity filter).
 template <class P, int NT>
 __global__ void __launch_bounds__(NT) helicity_kernel(const double* __restrict__ mom, long long nevt,
@@ -203,6 +308,11 @@ struct LaunchArgs {
   const void* ctile;  // FP16 colour-matrix operand tile (tensor-core path)
   unsigned* status;
   cudaStream_t stream;
+  // event-by-event helicity and colour choice (select kernels only)
+  const double* rnd;
+  int* hel_out;
+  int* col_out;
+  double* colw_out;
 };
 
 template <class K>
@@ -219,6 +329,30 @@ int launch_sigma(const LaunchArgs& a) {
   const long long grid = (a.nevt + NT - 1) / NT;
   sigma_kernel<P, R, NT><<<(unsigned)grid, NT, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels, a.nhel, a.kp,
                                                                   a.status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <class P, typename R, int NT>
+int launch_select(const LaunchArgs& a) {
+  constexpr size_t smem = Layout<P, R, NT>::base_bytes;
+  static const cudaError_t attr = set_smem_attr(select_kernel<P, R, NT>, smem);
+  if (attr != cudaSuccess) return -4;
+  if (a.nevt <= 0) return 0;
+  const long long grid = (a.nevt + NT - 1) / NT;
+  select_kernel<P, R, NT><<<(unsigned)grid, NT, smem, a.stream>>>(a.mom, a.nevt, a.rnd, a.out, a.hel_out, a.col_out,
+                                                                   a.colw_out, a.hels, a.nhel, a.kp, a.status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <class P, int NT>
+int launch_sigma_paper(const LaunchArgs& a) {
+  constexpr size_t smem = Layout<P, double, NT>::base_bytes;
+  static const cudaError_t attr = set_smem_attr(sigma_paper_kernel<P, NT>, smem);
+  if (attr != cudaSuccess) return -4;
+  if (a.nevt <= 0) return 0;
+  const long long grid = (a.nevt + NT - 1) / NT;
+  sigma_paper_kernel<P, NT><<<(unsigned)grid, NT, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels, a.nhel, a.kp,
+                                                                     static_cast<const short*>(a.ctile), a.status);
   return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
@@ -245,6 +379,9 @@ struct ProcDesc {
   int (*sigma_mixed)(const LaunchArgs&);
   int (*helicities)(const LaunchArgs&);
   int tc_k;  // > 0: the mixed path contracts colour on the tensor cores, K = N = tc_k
+  int (*select_fp64)(const LaunchArgs&);
+  int (*select_mixed)(const LaunchArgs&);
+  int (*sigma_paper)(const LaunchArgs&);
 };
 
 }  // namespace mg

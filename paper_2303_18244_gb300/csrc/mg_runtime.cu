@@ -97,7 +97,7 @@ extern "C" int mg_process_create(const char* proc, const mg_params* p, mg_proces
   if (!proc || !p) return MG_ERR_ARG;
   const ProcDesc* d = mg::find_process(proc);
   if (!d) return MG_ERR_PROC;
-  if (p->precision != MG_FP64 && p->precision != MG_MIXED) return MG_ERR_ARG;
+  if (p->precision != MG_FP64 && p->precision != MG_MIXED && p->precision != MG_MIXED_PAPER) return MG_ERR_ARG;
   KParams kp;
   int rc = make_kparams(d, *p, kp);
   if (rc) return rc;
@@ -140,11 +140,27 @@ extern "C" int mg_process_create(const char* proc, const mg_params* p, mg_proces
       return MG_ERR_CUDA;
     }
   }
+  if (p->precision == MG_MIXED_PAPER) {
+    // colour numerators for the FP32 colour sum: K_ii and 2 K_ij (j > i)
+    std::vector<short> kt((size_t)d->ncol * d->ncol, 0);
+    for (int i = 0; i < d->ncol; i++)
+      for (int j = i; j < d->ncol; j++) kt[(size_t)i * d->ncol + j] = (short)(i == j ? d->knum[i * d->ncol + j]
+                                                                                   : 2 * d->knum[i * d->ncol + j]);
+    if (cudaMalloc(&h->d_ctile, kt.size() * sizeof(short)) != cudaSuccess) {
+      mg_process_destroy(h);
+      return MG_ERR_NOMEM;
+    }
+    if (cudaMemcpy(h->d_ctile, kt.data(), kt.size() * sizeof(short), cudaMemcpyHostToDevice) != cudaSuccess) {
+      mg_process_destroy(h);
+      return MG_ERR_CUDA;
+    }
+  }
   // one-time kernel attributes (no launch for nevt = 0), so that later calls
   // can be captured into CUDA graphs
   LaunchArgs a{};
   a.nevt = 0;
-  if (d->sigma_fp64(a) || d->sigma_mixed(a) || d->helicities(a)) {
+  if (d->sigma_fp64(a) || d->sigma_mixed(a) || d->helicities(a) || d->select_fp64(a) || d->select_mixed(a) ||
+      d->sigma_paper(a)) {
     mg_process_destroy(h);
     return MG_ERR_CUDA;
   }
@@ -186,7 +202,9 @@ int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, 
   a.ctile = h->d_ctile;
   a.status = h->d_status;
   a.stream = stream;
-  const int rc = (h->par.precision == MG_MIXED) ? h->d->sigma_mixed(a) : h->d->sigma_fp64(a);
+  const int rc = h->par.precision == MG_MIXED         ? h->d->sigma_mixed(a)
+                 : h->par.precision == MG_MIXED_PAPER ? h->d->sigma_paper(a)
+                                                      : h->d->sigma_fp64(a);
   return rc ? MG_ERR_CUDA : MG_OK;
 }
 
@@ -196,6 +214,32 @@ extern "C" int mg_sigma(mg_process* h, const double* momenta_dev, int64_t nevt, 
   if (!momenta_dev || !me_out_dev || !aligned16(momenta_dev)) return MG_ERR_ARG;
   DeviceGuard g(h->device);
   return mg_launch_sigma(h, momenta_dev, nevt, me_out_dev, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int mg_sigma_select(mg_process* h, const double* momenta_dev, int64_t nevt, const double* rnd_dev,
+                               double* me_out_dev, int* hel_out_dev, int* col_out_dev, double* colw_out_dev,
+                               void* stream) {
+  if (!h || nevt < 0) return MG_ERR_ARG;
+  if (nevt == 0) return MG_OK;
+  if (!momenta_dev || !rnd_dev || !me_out_dev || !hel_out_dev || !col_out_dev || !aligned16(momenta_dev))
+    return MG_ERR_ARG;
+  DeviceGuard g(h->device);
+  LaunchArgs a{};
+  a.mom = momenta_dev;
+  a.nevt = nevt;
+  a.out = me_out_dev;
+  a.hels = h->d_hels;
+  a.nhel = h->n_good;
+  a.kp = h->kp;
+  a.status = h->d_status;
+  a.stream = static_cast<cudaStream_t>(stream);
+  a.rnd = rnd_dev;
+  a.hel_out = hel_out_dev;
+  a.col_out = col_out_dev;
+  a.colw_out = colw_out_dev;
+  // the paper-style mode chooses from its FP64 amplitudes
+  const int rc = (h->par.precision == MG_MIXED) ? h->d->select_mixed(a) : h->d->select_fp64(a);
+  return rc ? MG_ERR_CUDA : MG_OK;
 }
 
 extern "C" int mg_sigma_helicities(mg_process* h, const double* momenta_dev, int64_t nevt, double* out_dev,

@@ -19,6 +19,8 @@ the index is set, -1 otherwise (index 0 = all negative).
 """
 from __future__ import annotations
 
+import os
+
 from .colour import colour_matrix_exact, common_denominator, words
 from .diagrams import build_plan, count_diagrams
 
@@ -110,8 +112,10 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     S.alloc("ft", 5)
     S.alloc("ftb", 5)
     nslot = S.n
-    # table mode, FP32 path: every gluon-subset momentum sum, precomputed per event
-    if mode == "table":
+    # table mode, FP32 path: every gluon-subset momentum sum precomputed per event
+    # (off: the larger slab halves the CTAs per SM, measured slower)
+    ktable = mode == "table" and os.environ.get("MG_TABLE_KSUMS", "0") == "1"
+    if ktable:
         for m in range(1, full + 1):
             S.alloc(f"K{m}", 4)
     nslot_k = S.n
@@ -130,7 +134,7 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     L.append(f"static constexpr int NAMP = {len(plan.amps)};")
     L.append(f"static constexpr int NSLOT = {nslot};")
     L.append(f"static constexpr int NSLOT_K = {nslot_k};  // + precomputed subset momenta (table mode, FP32)")
-    L.append(f"static constexpr int KBASE = {sl['K1'] if mode == 'table' else 0};")
+    L.append(f"static constexpr int KBASE = {sl['K1'] if ktable else 0};")
     L.append(f"static constexpr int NSLOT_LEAN = {nslot_lean};  // slots without the external-state ingredients")
     L.append("// FP32 path: recompute the external-state ingredients per helicity instead of")
     L.append("// keeping them in shared memory (measured slower while registers bound occupancy)")
@@ -186,7 +190,7 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
     L.append("    const double P2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];")
     L.append(f"    EV({sl['cgtt']}) = R(g / P2); }}")
-    if mode == "table":
+    if ktable:
         L.append("  if constexpr (sizeof(R) == 4) {")
         for m in range(1, full + 1):
             comps = ksum_fp64(m)
@@ -471,12 +475,39 @@ def _ext_top_lines(name, kind, sl, declare, wrap=False):
     return L
 
 
-def program(plan) -> list[tuple[str, int]]:
+def colour_patterns(plan):
+    """Group amplitude terms whose colour coefficients agree up to an overall
+    sign: returns (pattern of each amp, sign of each amp relative to its
+    pattern, list of canonical patterns as sorted (flow, coeff) tuples)."""
+    pats, pid, sign = [], [], []
+    index = {}
+    for op, co in plan.amps:
+        t = tuple(sorted(co.items()))
+        neg = tuple(sorted((k, -c) for k, c in co.items()))
+        key = min(t, neg)
+        if key not in index:
+            index[key] = len(pats)
+            pats.append(key)
+        pid.append(index[key])
+        sign.append(1 if t == key else -1)
+    return pid, sign, pats
+
+
+def program(plan, by_pattern: bool = False) -> list[tuple[str, int]]:
     """Linear evaluation order: ("cur", id) on first use, ("amp", index) --
-    the order in which the straight-line emitter writes the code."""
+    the order in which the straight-line emitter writes the code.  With
+    by_pattern, amplitudes sharing a colour pattern are made consecutive
+    (patterns in order of first appearance in the schedule)."""
     seq = []
     done = set()
     gtt = plan.keys.get(("gtt",))
+    order = schedule(plan)
+    if by_pattern:
+        pid, _, _ = colour_patterns(plan)
+        first = {}
+        for pos, ai in enumerate(order):
+            first.setdefault(pid[ai], pos)
+        order = sorted(order, key=lambda ai: (first[pid[ai]], order.index(ai)))
 
     def cur(c):
         if c in done:
@@ -497,7 +528,7 @@ def program(plan) -> list[tuple[str, int]]:
         done.add(c)
         seq.append(("cur", c))
 
-    for ai in schedule(plan):
+    for ai in order:
         op = plan.amps[ai][0]
         if op[0] == "f":
             cur(op[1]); cur(op[2]); cur(op[3])
@@ -511,7 +542,20 @@ def program(plan) -> list[tuple[str, int]]:
 
 def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
     """Op table + interpreter-driven amplitudes() and a looped colour form."""
-    seq = program(plan)
+    # amplitudes grouped by colour pattern (fewer colour-flow updates, a larger
+    # current store); MG_TABLE_GROUP=0 keeps the register-pressure order
+    by_pattern = os.environ.get("MG_TABLE_GROUP", "1") != "0"
+    seq = program(plan, by_pattern=by_pattern)
+    pid, psign, pats = colour_patterns(plan)
+    if not by_pattern:  # every amplitude its own group
+        pats = [tuple(sorted(co.items())) for op, co in plan.amps]
+        pid = list(range(len(plan.amps)))
+        psign = [1] * len(plan.amps)
+    amp_positions = [i for kind, i in seq if kind == "amp"]
+    last_of_pattern = {}
+    for ai in amp_positions:
+        last_of_pattern[pid[ai]] = ai
+    pat_jl = {}
     gtt = plan.keys.get(("gtt",))
     # inputs of every step, for liveness
     def inputs(kind, i):
@@ -555,11 +599,17 @@ def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
                 assert k in ext_kinds
         else:
             op, co = plan.amps[i]
-            j0 = len(jl)
-            for f, c in sorted(co.items()):
-                assert c in (1, -1), c
-                jl.append((f << 1) | (1 if c < 0 else 0))
-            nj = len(jl) - j0
+            # amplitudes of one colour pattern are consecutive: accumulate them
+            # (with their sign relative to the pattern) and apply the pattern's
+            # flow list once, after the last of them (njl = 0 before that)
+            j0, nj = 0, 0
+            if last_of_pattern[pid[i]] == i:
+                j0 = len(jl)
+                for f, c in pats[pid[i]]:
+                    assert c in (1, -1), c
+                    jl.append((f << 1) | (1 if c < 0 else 0))
+                nj = len(jl) - j0
+            sg = 1 if psign[i] > 0 else 0
             if op[0] == "f":
                 ops.append([6, slot[op[1]], slot[op[2]], slot[op[3]], 0, 0, j0, nj])
             elif op[0] == "a3":
@@ -567,6 +617,7 @@ def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
                             j0, nj])
             else:
                 ops.append([8, slot[op[1]], slot[op[2]], slot[op[3]], op[4], slot[gtt], j0, nj])
+            ops[-1][0] |= (sg << 8)  # bit 8 of the type word: +1 (set) or -1 relative sign
         for d in inputs(kind, i):
             if last[d] == t and plan.ops[d][0] not in ext_kinds:
                 free.append(slot[d])
@@ -605,17 +656,21 @@ def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
     L.append("template <typename R>")
     L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
     L.append(f"  const short* __restrict__ knum = {tag}_KNUM;")
+    L.append("  // symmetric: diagonal once, off-diagonal pairs j > i twice (knum holds 2 K_ij there)")
     L.append("  R acc = R(0);")
     L.append("#pragma unroll 1")
     L.append(f"  for (int i = 0; i < {ncol}; i++) {{")
-    L.append("    R yr = R(0), yi = R(0);")
-    L.append(f"    for (int j = 0; j < {ncol}; j++) {{")
-    L.append(f"      const R k = R(__ldg(knum + i * {ncol} + j));")
-    L.append("      yr = fmaf_t<R>(k, jamp[j * js].re, yr);")
-    L.append("      yi = fmaf_t<R>(k, jamp[j * js].im, yi);")
+    L.append("    const cx<R> ji = jamp[i * js];")
+    L.append(f"    const short* row = knum + i * {ncol};")
+    L.append("    R yr = R(__ldg(row + i)) * ji.re, yi = R(__ldg(row + i)) * ji.im;")
+    L.append(f"    for (int j = i + 1; j < {ncol}; j++) {{")
+    L.append("      const R k = R(__ldg(row + j));")
+    L.append("      const cx<R> jj = jamp[j * js];")
+    L.append("      yr = fmaf_t<R>(k, jj.re, yr);")
+    L.append("      yi = fmaf_t<R>(k, jj.im, yi);")
     L.append("    }")
-    L.append("    acc = fmaf_t<R>(jamp[i * js].re, yr, acc);")
-    L.append("    acc = fmaf_t<R>(jamp[i * js].im, yi, acc);")
+    L.append("    acc = fmaf_t<R>(ji.re, yr, acc);")
+    L.append("    acc = fmaf_t<R>(ji.im, yi, acc);")
     L.append("  }")
     L.append("  return acc;")
     L.append("}")
@@ -626,7 +681,9 @@ def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
         table_src.append(f"  {{{o[0]}, {o[1]}, {o[2]}, {o[3]}}}, {{{o[4]}, {o[5]}, {o[6]}, {o[7]}}},")
     table_src.append("};")
     table_src.append(f"static __device__ const short {tag}_JL[{len(jl)}] = {{{', '.join(map(str, jl))}}};")
-    table_src.append(f"static __device__ const short {tag}_KNUM[{ncol * ncol}] = {{{_fmt_knum(K)}}};")
+    # upper triangle doubled (the symmetric loop reads K_ii and 2 K_ij, j > i); |2 K| <= 8192 fits a short
+    KS = [[K[i][j] if i == j else (2 * K[i][j] if j > i else 0) for j in range(ncol)] for i in range(ncol)]
+    table_src.append(f"static __device__ const short {tag}_KNUM[{ncol * ncol}] = {{{_fmt_knum(KS)}}};")
     _TABLES[tag] = table_src
     return L
 
@@ -765,10 +822,32 @@ namespace mg {{
 static int sigma_fp64(const LaunchArgs& a) {{ return launch_sigma<{tag}, double, {nt64}>(a); }}
 static int sigma_mixed(const LaunchArgs& a) {{ return {mixed}; }}
 static int helicities(const LaunchArgs& a) {{ return launch_helicities<{tag}, {nt64}>(a); }}
+int select_{tag}_fp64(const LaunchArgs& a);
+int select_{tag}_mixed(const LaunchArgs& a);
+int paper_{tag}(const LaunchArgs& a);
 static const ProcDesc desc = {{"{proc}", "{tag}", {tag}::NPAR, {tag}::NHEL, {tag}::NCOL, {tag}::NDIAG,
                               {tag}::NAMP, {tag}::IDEN, {tag}::CDEN, {tag}::KNUM,
-                              sigma_fp64, sigma_mixed, helicities, {tck}}};
+                              sigma_fp64, sigma_mixed, helicities, {tck},
+                              select_{tag}_fp64, select_{tag}_mixed, paper_{tag}}};
 const ProcDesc* proc_{tag}() {{ return &desc; }}
+}}  // namespace mg
+"""
+    return tag, src
+
+
+def emit_select_tu(proc: str) -> tuple[str, str]:
+    """Translation unit of the helicity/colour-choice kernels and of the
+    paper-style mixed kernel (compiled in parallel with the main kernels)."""
+    tag, _ = PROCESSES[proc]
+    nt64, nt32 = THREADS[tag]
+    src = f"""// generated by paper_2303_18244_gb300.generator: helicity/colour choice kernels of '{proc}'
+#include "../mg_kernels.cuh"
+#include "{tag}.cuh"
+
+namespace mg {{
+int select_{tag}_fp64(const LaunchArgs& a) {{ return launch_select<{tag}, double, {nt64}>(a); }}
+int select_{tag}_mixed(const LaunchArgs& a) {{ return launch_select<{tag}, float, {nt32}>(a); }}
+int paper_{tag}(const LaunchArgs& a) {{ return launch_sigma_paper<{tag}, {nt64}>(a); }}
 }}  // namespace mg
 """
     return tag, src

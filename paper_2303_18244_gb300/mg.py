@@ -20,6 +20,7 @@ MG_OK = 0
 MG_PENDING = 1
 MG_FP64 = 0
 MG_MIXED = 1
+MG_MIXED_PAPER = 2
 MG_NO_TOP_WIDTH = 1
 MG_PHOTON_ONLY = 2
 
@@ -27,7 +28,7 @@ MG_PHOTON_ONLY = 2
 EXPORTS = (
     "mg_params_default", "mg_process_create", "mg_process_destroy", "mg_process_info",
     "mg_good_helicities", "mg_sigma", "mg_sigma_host", "mg_process_status", "mg_sigma_helicities",
-    "mg_good_helicities_static", "mg_rambo",
+    "mg_good_helicities_static", "mg_rambo", "mg_sigma_select",
     "mg_server_cfg_default", "mg_server_create", "mg_server_submit", "mg_server_poll",
     "mg_server_destroy", "mg_strerror",
     # include/mg_diag.h
@@ -80,6 +81,7 @@ def lib() -> ctypes.CDLL:
         L.mg_good_helicities_static.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
         L.mg_sigma.argtypes = [vp, vp, i64, vp, vp]
         L.mg_rambo.argtypes = [vp, ctypes.c_double, ctypes.c_uint64, i64, i64, vp, vp]
+        L.mg_sigma_select.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
         L.mg_sigma_host.argtypes = [vp, vp, i64, vp, vp]
         L.mg_process_status.argtypes = [vp]
         L.mg_sigma_helicities.argtypes = [vp, vp, i64, vp, vp]
@@ -212,6 +214,21 @@ def rambo(h: Process, sqrt_s: float, seed: int, first_event: int, momenta_dev, s
     nevt = momenta_dev.shape[0]
     _check(lib().mg_rambo(h.handle, sqrt_s, seed, first_event, nevt, _dev_check(momenta_dev),
                           _stream_ptr(stream)), "mg_rambo")
+
+
+def sigma_select(h: Process, momenta_dev, rnd_dev, me_out_dev, hel_out_dev, col_out_dev, colw_out_dev=None,
+                 stream=None):
+    """mg_sigma_select: ME plus the per-event helicity and colour-flow choice.
+    rnd_dev: float64 [nevt][2]; hel/col outputs: int32 [nevt]; colw: float64 [nevt][n_col] or None."""
+    import torch
+    nevt = momenta_dev.shape[0]
+    for t in (hel_out_dev, col_out_dev):
+        if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+            raise TypeError("expected contiguous int32 CUDA tensors for the choices")
+    _check(lib().mg_sigma_select(h.handle, _dev_check(momenta_dev), nevt, _dev_check(rnd_dev), _dev_check(me_out_dev),
+                                 hel_out_dev.data_ptr(), col_out_dev.data_ptr(),
+                                 _dev_check(colw_out_dev) if colw_out_dev is not None else None,
+                                 _stream_ptr(stream)), "mg_sigma_select")
 
 
 def sigma_helicities(h: Process, momenta_dev, out_dev, stream=None):

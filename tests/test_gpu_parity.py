@@ -227,3 +227,16 @@ def test_photon_only_closed_form():
     a, b = p[:, 1, 1:], p[:, 3, 1:]
     c = (a * b).sum(-1) / np.linalg.norm(a, axis=1) / np.linalg.norm(b, axis=1)
     np.testing.assert_allclose(got, e2 ** 2 * (1 + c ** 2), rtol=1e-12)
+
+
+@pytest.mark.parametrize("proc", PROCS, ids=_ids)
+def test_paper_mixed_parity_small(proc):
+    """The paper's mixed mode: FP64 diagrams, FP32 colour algebra."""
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, n, _ = WORKLOADS[proc]
+    p = process_momenta(proc, rs, n, seed)
+    h = mg.Process(proc, precision=mg.MG_MIXED_PAPER)
+    got = _gpu_me(h, p)
+    r = _rel(got, O.me(proc, p))
+    assert np.median(r) <= 1e-6 and r.max() <= 1e-4
