@@ -267,6 +267,8 @@ def main():
         mg.sigma_host(hmix, hp, ho, stream)
     e2e_ms = []
     for _ in range(max(3, args.steps // 2)):
+        flush.zero_()  # same L2 state as the device-timed steps
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         mg.sigma_host(hmix, hp, ho, stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)

@@ -234,3 +234,13 @@ def ordered_colour_sum(n, kin, eps, pt, ubar, ptb, v, params: Params | None = No
 def dressed_colour_sum(n, kin, eps, pt, ubar, ptb, v, params: Params | None = None) -> float:
     out = np.empty(1, dtype=np.float64)
     return float(_qline_call(lib().mgo_dressed_colour_sum, n, params, kin, eps, pt, ubar, ptb, v, out)[0])
+
+
+def unweight(w: np.ndarray, r: np.ndarray, w_max: float) -> np.ndarray:
+    """Hit-or-miss unweighting (paper Sect. 2, a serial step after the ME):
+    the indices i, in increasing order, of the events with r_i * w_max < w_i,
+    r_i uniform in [0, 1).  Written as the definition, one event at a time."""
+    w = np.asarray(w, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    kept = [i for i in range(w.shape[0]) if r[i] * w_max < w[i]]
+    return np.array(kept, dtype=np.int64)

@@ -25,7 +25,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 # extra nvcc flags (e.g. -DMG_TC_MINB=3 for a launch-shape sweep)
 FLAGS += os.environ.get("MG_NVCC_EXTRA", "").split()
 
-HAND = ["mg_runtime.cu", "mg_server.cu", "mg_diag.cu", "mg_static.cu", "mg_phasespace.cu"]
+HAND = ["mg_runtime.cu", "mg_server.cu", "mg_diag.cu", "mg_static.cu", "mg_phasespace.cu", "mg_unweight.cu"]
 
 
 def _write_if_changed(path: str, text: str) -> None:
@@ -51,9 +51,9 @@ def processes() -> list[str]:
 
 
 def generate() -> list[str]:
-    """Write csrc/gen/<tag>.cuh, <tag>_kernels.cu and registry.cu; return the TUs."""
+    """Write csrc/gen/<tag>.cuh, <tag>_f64.cu, <tag>_f32.cu and registry.cu; return the TUs."""
     sys.path.insert(0, ROOT)
-    from paper_2303_18244_gb300.generator.emit import PROCESSES, emit, emit_kernels_tu, emit_select_tu
+    from paper_2303_18244_gb300.generator.emit import PROCESSES, emit, emit_tu
     os.makedirs(GEN, exist_ok=True)
     tus = []
     procs = processes()
@@ -69,14 +69,11 @@ def generate() -> list[str]:
     for proc in procs:
         tag, hdr = emit(proc)
         _write_if_changed(os.path.join(GEN, f"{tag}.cuh"), hdr)
-        _, tu = emit_kernels_tu(proc)
-        path = os.path.join(GEN, f"{tag}_kernels.cu")
-        _write_if_changed(path, tu)
-        tus.append(path)
-        _, tu = emit_select_tu(proc)
-        path = os.path.join(GEN, f"{tag}_select.cu")
-        _write_if_changed(path, tu)
-        tus.append(path)
+        for prec in ("f64", "f32"):
+            _, tu = emit_tu(proc, prec)
+            path = os.path.join(GEN, f"{tag}_{prec}.cu")
+            _write_if_changed(path, tu)
+            tus.append(path)
     return tus
 
 
@@ -111,7 +108,7 @@ def build(verbose: bool = True) -> str:
     tus = generate() + [os.path.join(CSRC, f) for f in HAND]
     # largest units first so that they start early
     def weight(p):
-        for suf in ("_kernels.cu", "_select.cu"):
+        for suf in ("_f64.cu", "_f32.cu"):
             if p.endswith(suf):
                 return -os.path.getsize(p.replace(suf, ".cuh"))
         return 0

@@ -151,8 +151,7 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
 
   const int nvalid =
       load_and_prepare_at<P, float, NT>(tma_bar, reinterpret_cast<double*>(region), slab, mom, nevt, kp, status);
-  if (nvalid < 0) return;
-  __syncthreads();  // every thread is done with the momenta tile: reuse its space
+  if (nvalid < 0) return;  // (load_and_prepare_at ends with a block barrier: the tile space is free)
 
   // colour matrix tile (constant), operand tiles, accumulators
   unsigned char* atile = region;                    // 4 tiles: re_hi, re_lo, im_hi, im_lo

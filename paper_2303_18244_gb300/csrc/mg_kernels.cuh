@@ -87,7 +87,7 @@ constexpr uint32_t WAIT_POLLS = 1u << 22;
 // ingredients, which the FP32 code then recomputes per helicity)
 template <class P, typename R>
 constexpr int slab_slots() {
-  return sizeof(R) == 4 ? (P::LEAN_SLAB ? P::NSLOT_LEAN : P::NSLOT_K) : P::NSLOT;
+  return (sizeof(R) == 4 && P::LEAN_SLAB) ? P::NSLOT_LEAN : P::NSLOT;
 }
 
 template <class P, typename R, int NT>
@@ -96,9 +96,13 @@ struct Layout {
   static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
   static constexpr size_t slab_bytes = size_t(NT) * slab_slots<P, R>() * sizeof(R);
   static constexpr size_t jamp_bytes = size_t(NT) * P::NCOL * sizeof(cx<R>);
-  static constexpr size_t slab_off = bar_bytes + ((stage_bytes + 127) / 128) * 128;
+  static constexpr size_t slab_off = bar_bytes;
   static constexpr size_t jamp_off = slab_off + ((slab_bytes + 127) / 128) * 128;
-  static constexpr size_t base_bytes = jamp_off + ((jamp_bytes + 127) / 128) * 128;
+  // the momenta tile is staged in the colour-flow space: only prepare reads
+  // it, and a block barrier separates that from the first flow update
+  static constexpr size_t stage_off = jamp_off;
+  static constexpr size_t union_bytes = stage_bytes > jamp_bytes ? stage_bytes : jamp_bytes;
+  static constexpr size_t base_bytes = jamp_off + ((union_bytes + 127) / 128) * 128;
 };
 
 // A1 + A2: stage the tile, run the per-event FP64 set-up into the slab.
@@ -131,6 +135,7 @@ __device__ __forceinline__ int load_and_prepare_at(uint64_t* bar, double* stage,
   }
   const int le = tid < nvalid ? tid : nvalid - 1;  // ragged tail: repeat a valid event
   P::template prepare<R>(stage + le * P::NPAR * 4, kp.v, slab + tid, NT);
+  __syncthreads();  // every thread is done with the momenta tile (its space is reused)
   return nvalid;
 }
 
@@ -139,7 +144,7 @@ __device__ __forceinline__ int load_and_prepare(unsigned char* smem, const doubl
                                                 const KParams& kp, unsigned* status) {
   using LY = Layout<P, R, NT>;
   return load_and_prepare_at<P, R, NT>(reinterpret_cast<uint64_t*>(smem),
-                                       reinterpret_cast<double*>(smem + LY::bar_bytes),
+                                       reinterpret_cast<double*>(smem + LY::stage_off),
                                        reinterpret_cast<R*>(smem + LY::slab_off), mom, nevt, kp, status);
 }
 

@@ -20,10 +20,18 @@
 #include <stdint.h>
 
 // MG_VERTEX: inlining of the vertex routines (ffv_*, vvv_*, vvvv_*).  Inlined
-// by default; a translation unit may define it as __noinline__ to compile very
-// large processes as a sequence of calls.
+// by default; a translation unit may define it as __noinline__, which turns a
+// large process's straight-line helicity program into a sequence of calls to
+// a few small routines that stay in the instruction cache (the inlined
+// program is hundreds of KB of machine code, fetched again for every
+// helicity).  Arguments are passed by value so that calls keep them in
+// registers.
 #ifndef MG_VERTEX
 #define MG_VERTEX __forceinline__
+#endif
+// MG_VERTEX_AMP: the same for the amplitude routines (ffv_amp, vvv_amp, vvvv_amp)
+#ifndef MG_VERTEX_AMP
+#define MG_VERTEX_AMP MG_VERTEX
 #endif
 
 namespace mg {
@@ -90,6 +98,24 @@ template <typename R>
 struct Sp {  // Weyl-basis 4-spinor (row or column)
   cx<R> c[4];
 };
+// a current kept in a V4-typed store slot and read back as a spinor (and back)
+template <typename R>
+__device__ __forceinline__ Sp<R> as_sp(const V4<R>& w) {
+  Sp<R> s;
+  for (int i = 0; i < 4; i++) s.c[i] = w.c[i];
+  return s;
+}
+template <typename R>
+__device__ __forceinline__ V4<R> as_v4(const Sp<R>& s) {
+  V4<R> w;
+  for (int i = 0; i < 4; i++) w.c[i] = s.c[i];
+  return w;
+}
+template <typename R>
+struct M4 {  // real 4-vector (a momentum), passed by value like V4 and Sp
+  R v[4];
+  __host__ __device__ constexpr R operator[](int i) const { return v[i]; }
+};
 
 // Minkowski products
 template <typename R>
@@ -101,7 +127,7 @@ __device__ __forceinline__ cx<R> dot(const V4<R>& a, const V4<R>& b) {
   return s;
 }
 template <typename R>
-__device__ __forceinline__ cx<R> dot(const R k[4], const V4<R>& b) {
+__device__ __forceinline__ cx<R> dot(const M4<R> k, const V4<R>& b) {
   return {k[0] * b.c[0].re - k[1] * b.c[1].re - k[2] * b.c[2].re - k[3] * b.c[3].re,
           k[0] * b.c[0].im - k[1] * b.c[1].im - k[2] * b.c[2].im - k[3] * b.c[3].im};
 }
@@ -320,7 +346,7 @@ __device__ __forceinline__ void sigma_blocks(const V4<R>& J, cx<R> X[4], cx<R> Y
 }
 // same for a real momentum Q
 template <typename R>
-__device__ __forceinline__ void sigma_blocks(const R Q[4], cx<R> X[4], cx<R> Y[4]) {
+__device__ __forceinline__ void sigma_blocks(const M4<R> Q, cx<R> X[4], cx<R> Y[4]) {
   X[0] = {Q[0] - Q[3], R(0)};
   X[1] = {-Q[1], Q[2]};
   X[2] = {-Q[1], -Q[2]};
@@ -345,7 +371,7 @@ __device__ __forceinline__ void mulcol(const cx<R> M[4], cx<R> c0, cx<R> c1, cx<
 
 // Fbar Jslash F
 template <typename R>
-__device__ MG_VERTEX cx<R> ffv_amp(const Sp<R>& a, const V4<R>& J, const Sp<R>& b) {
+__device__ MG_VERTEX_AMP cx<R> ffv_amp(const Sp<R> a, const V4<R> J, const Sp<R> b) {
   cx<R> X[4], Y[4];
   sigma_blocks(J, X, Y);
   cx<R> t0, t1, u0, u1;
@@ -356,7 +382,7 @@ __device__ MG_VERTEX cx<R> ffv_amp(const Sp<R>& a, const V4<R>& J, const Sp<R>& 
 
 // row current: coef * Fbar Jslash (Qslash + m)
 template <typename R>
-__device__ MG_VERTEX Sp<R> ffv_row(const Sp<R>& a, const V4<R>& J, const R Q[4], R m, cx<R> coef) {
+__device__ MG_VERTEX Sp<R> ffv_row(const Sp<R> a, const V4<R> J, const M4<R> Q, R m, cx<R> coef) {
   cx<R> X[4], Y[4], XQ[4], YQ[4];
   sigma_blocks(J, X, Y);
   sigma_blocks(Q, XQ, YQ);
@@ -376,7 +402,7 @@ __device__ MG_VERTEX Sp<R> ffv_row(const Sp<R>& a, const V4<R>& J, const R Q[4],
 
 // column current: coef * (qslash + m) Jslash F
 template <typename R>
-__device__ MG_VERTEX Sp<R> ffv_col(const V4<R>& J, const Sp<R>& b, const R q[4], R m, cx<R> coef) {
+__device__ MG_VERTEX Sp<R> ffv_col(const V4<R> J, const Sp<R> b, const M4<R> q, R m, cx<R> coef) {
   cx<R> X[4], Y[4], XQ[4], YQ[4];
   sigma_blocks(J, X, Y);
   sigma_blocks(q, XQ, YQ);
@@ -396,7 +422,7 @@ __device__ MG_VERTEX Sp<R> ffv_col(const V4<R>& J, const Sp<R>& b, const R q[4],
 
 // vector current coef * Fbar gamma^mu (cL PL + cR PR) F
 template <typename R>
-__device__ MG_VERTEX V4<R> ffv_vcur(const Sp<R>& a, const Sp<R>& b, cx<R> coef, R cL = R(1), R cR = R(1)) {
+__device__ MG_VERTEX V4<R> ffv_vcur(const Sp<R> a, const Sp<R> b, cx<R> coef, R cL = R(1), R cR = R(1)) {
   // upper: (a0,a1) sigma^mu (b2,b3) [right-handed F], lower: (a2,a3) sigmabar^mu (b0,b1)
   const cx<R> u02 = a.c[0] * b.c[2], u13 = a.c[1] * b.c[3], u03 = a.c[0] * b.c[3], u12 = a.c[1] * b.c[2];
   const cx<R> l20 = a.c[2] * b.c[0], l31 = a.c[3] * b.c[1], l21 = a.c[2] * b.c[1], l30 = a.c[3] * b.c[0];
@@ -412,11 +438,11 @@ __device__ MG_VERTEX V4<R> ffv_vcur(const Sp<R>& a, const Sp<R>& b, cx<R> coef, 
 // three-gluon current: c * V3(kx, Jx, ky, Jy),
 //   V3 = (Jx.Jy)(kx-ky) + Jy (2ky+kx).Jx - Jx (2kx+ky).Jy
 template <typename R>
-__device__ MG_VERTEX V4<R> vvv_cur(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy, R c) {
-  R a[4], b[4];
+__device__ MG_VERTEX V4<R> vvv_cur(const M4<R> kx, const V4<R> Jx, const M4<R> ky, const V4<R> Jy, R c) {
+  M4<R> a, b;
   for (int mu = 0; mu < 4; mu++) {
-    a[mu] = R(2) * ky[mu] + kx[mu];
-    b[mu] = R(2) * kx[mu] + ky[mu];
+    a.v[mu] = R(2) * ky[mu] + kx[mu];
+    b.v[mu] = R(2) * kx[mu] + ky[mu];
   }
   const cx<R> xy = dot(Jx, Jy);
   const cx<R> ax = dot(a, Jx);
@@ -432,13 +458,13 @@ __device__ MG_VERTEX V4<R> vvv_cur(const R kx[4], const V4<R>& Jx, const R ky[4]
 }
 // amplitude: c * V3(kx, Jx, ky, Jy) . G
 template <typename R>
-__device__ MG_VERTEX cx<R> vvv_amp(const R kx[4], const V4<R>& Jx, const R ky[4], const V4<R>& Jy,
-                                         const V4<R>& G, R c) {
-  R a[4], b[4], d[4];
+__device__ MG_VERTEX_AMP cx<R> vvv_amp(const M4<R> kx, const V4<R> Jx, const M4<R> ky, const V4<R> Jy,
+                                         const V4<R> G, R c) {
+  M4<R> a, b, d;
   for (int mu = 0; mu < 4; mu++) {
-    a[mu] = R(2) * ky[mu] + kx[mu];
-    b[mu] = R(2) * kx[mu] + ky[mu];
-    d[mu] = kx[mu] - ky[mu];
+    a.v[mu] = R(2) * ky[mu] + kx[mu];
+    b.v[mu] = R(2) * kx[mu] + ky[mu];
+    d.v[mu] = kx[mu] - ky[mu];
   }
   const cx<R> xy = dot(Jx, Jy);
   const cx<R> t = xy * dot(d, G) + dot(Jy, G) * dot(a, Jx) - dot(Jx, G) * dot(b, Jy);
@@ -448,7 +474,7 @@ __device__ MG_VERTEX cx<R> vvv_amp(const R kx[4], const V4<R>& Jx, const R ky[4]
 // four-gluon Lorentz structures for the three colour branches
 //   br 0: (X.Z) Y - (Y.Z) X     br 1: (X.Y) Z - (Y.Z) X     br 2: (X.Y) Z - (X.Z) Y
 template <int BR, typename R>
-__device__ MG_VERTEX V4<R> vvvv_cur(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, R c) {
+__device__ MG_VERTEX V4<R> vvvv_cur(const V4<R> X, const V4<R> Y, const V4<R> Z, R c) {
   V4<R> o;
   if (BR == 0) {
     const cx<R> xz = dot(X, Z), yz = dot(Y, Z);
@@ -463,7 +489,7 @@ __device__ MG_VERTEX V4<R> vvvv_cur(const V4<R>& X, const V4<R>& Y, const V4<R>&
   return o;
 }
 template <int BR, typename R>
-__device__ MG_VERTEX cx<R> vvvv_amp(const V4<R>& X, const V4<R>& Y, const V4<R>& Z, const V4<R>& G, R c) {
+__device__ MG_VERTEX_AMP cx<R> vvvv_amp(const V4<R> X, const V4<R> Y, const V4<R> Z, const V4<R> G, R c) {
   cx<R> t;
   if (BR == 0) t = dot(X, Z) * dot(Y, G) - dot(Y, Z) * dot(X, G);
   else if (BR == 1) t = dot(X, Y) * dot(Z, G) - dot(Y, Z) * dot(X, G);

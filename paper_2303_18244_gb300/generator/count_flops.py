@@ -31,6 +31,7 @@ PROGRAM = r"""
 #define __device__
 #define __host__
 #define __forceinline__ inline
+#define __noinline__
 #define __restrict__
 struct int4 { int x, y, z, w; };
 template <typename T> inline T __ldg(const T* p) { return *p; }

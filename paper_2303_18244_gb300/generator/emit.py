@@ -19,6 +19,7 @@ the index is set, -1 otherwise (index 0 = all negative).
 """
 from __future__ import annotations
 
+import math
 import os
 
 from .colour import colour_matrix_exact, common_denominator, words
@@ -112,13 +113,6 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     S.alloc("ft", 5)
     S.alloc("ftb", 5)
     nslot = S.n
-    # table mode, FP32 path: every gluon-subset momentum sum precomputed per event
-    # (off: the larger slab halves the CTAs per SM, measured slower)
-    ktable = mode == "table" and os.environ.get("MG_TABLE_KSUMS", "0") == "1"
-    if ktable:
-        for m in range(1, full + 1):
-            S.alloc(f"K{m}", 4)
-    nslot_k = S.n
     sl = S.names
 
     L = []
@@ -133,8 +127,6 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     L.append(f"static constexpr int NDIAG = {ndiag};")
     L.append(f"static constexpr int NAMP = {len(plan.amps)};")
     L.append(f"static constexpr int NSLOT = {nslot};")
-    L.append(f"static constexpr int NSLOT_K = {nslot_k};  // + precomputed subset momenta (table mode, FP32)")
-    L.append(f"static constexpr int KBASE = {sl['K1'] if ktable else 0};")
     L.append(f"static constexpr int NSLOT_LEAN = {nslot_lean};  // slots without the external-state ingredients")
     L.append("// FP32 path: recompute the external-state ingredients per helicity instead of")
     L.append("// keeping them in shared memory (measured slower while registers bound occupancy)")
@@ -190,21 +182,9 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
     L.append("    const double P2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];")
     L.append(f"    EV({sl['cgtt']}) = R(g / P2); }}")
-    if ktable:
-        L.append("  if constexpr (sizeof(R) == 4) {")
-        for m in range(1, full + 1):
-            comps = ksum_fp64(m)
-            for mu in range(4):
-                L.append(f"    EV({sl[f'K{m}'] + mu}) = R({comps[mu]});")
-        L.append("  }")
     L.append("#undef EV")
     L.append("}")
     L.append("")
-    if mode == "table":
-        L.extend(_table_sections(plan, tag, n, npar, ncol, sl, slots, full, K))
-        L.append(f"}};  // struct {tag}")
-        L.append("}  // namespace mg")
-        return "\n".join(L) + "\n"
     # ---------------- amplitudes ----------------
     L.append("// one helicity: currents and amplitudes, diagram by diagram, into the colour flows")
     L.append("template <typename R>")
@@ -228,11 +208,12 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         comps = []
         for mu in range(4):
             comps.append(" + ".join(f"EV({sl[f'k{i}'] + mu})" for i in idx))
-        L.append(f"  const R K{mask}[4] = {{{', '.join(comps)}}};")
+        L.append(f"  const M4<R> K{mask} = {{{{{', '.join(comps)}}}}};")
         emitted_k.add(mask)
         return f"K{mask}"
 
     emitted = {}
+    imports = {}  # chunked mode: currents produced by an earlier chunk -> store slot
 
     def cur(cid):
         """Emit current cid (and its dependencies) if not yet emitted; return its name."""
@@ -241,6 +222,13 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         op = plan.ops[cid]
         kind = op[0]
         name = f"w{cid}"
+        if cid in imports:
+            if kind in ("row", "col", "ubar", "v"):
+                L.append(f"  const Sp<R> {name} = as_sp(W[{imports[cid]}]);")
+            else:
+                L.append(f"  const V4<R> {name} = W[{imports[cid]}];")
+            emitted[cid] = name
+            return name
         if kind == "ext":
             i = op[1]
             L.extend(_ext_gluon_lines(name, i, slots[i], sl, declare=True))
@@ -268,8 +256,8 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             c = sl[f"cf{m}"]
             km = kname(m)
             L.append(f"  Sp<R> {name};")
-            L.append(f"  {{ const R Q[4] = {{EV({sl['pt']}) - {km}[0], EV({sl['pt'] + 1}) - {km}[1], "
-                     f"EV({sl['pt'] + 2}) - {km}[2], EV({sl['pt'] + 3}) - {km}[3]}};")
+            L.append(f"  {{ const M4<R> Q = {{{{EV({sl['pt']}) - {km}[0], EV({sl['pt'] + 1}) - {km}[1], "
+                     f"EV({sl['pt'] + 2}) - {km}[2], EV({sl['pt'] + 3}) - {km}[3]}}}};")
             L.append(f"    {name} = ffv_row<R>({npv}, {ng}, Q, mt, cx<R>{{EV({c}), EV({c + 1})}}); }}")
         elif kind == "col":
             gid, nxt, m = op[1], op[2], op[3]
@@ -277,8 +265,8 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             c = sl[f"cf{full ^ m}"]
             km = kname(m)
             L.append(f"  Sp<R> {name};")
-            L.append(f"  {{ const R q[4] = {{{km}[0] - EV({sl['ptb']}), {km}[1] - EV({sl['ptb'] + 1}), "
-                     f"{km}[2] - EV({sl['ptb'] + 2}), {km}[3] - EV({sl['ptb'] + 3})}};")
+            L.append(f"  {{ const M4<R> q = {{{{{km}[0] - EV({sl['ptb']}), {km}[1] - EV({sl['ptb'] + 1}), "
+                     f"{km}[2] - EV({sl['ptb'] + 2}), {km}[3] - EV({sl['ptb'] + 3})}}}};")
             L.append(f"    {name} = ffv_col<R>({ng}, {nn}, q, mt, cx<R>{{EV({c}), EV({c + 1})}}); }}")
         else:
             raise ValueError(kind)
@@ -286,7 +274,17 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         return name
 
     gtt_id = plan.keys.get(("gtt",))
-    for ai in schedule(plan):
+    # MG_LINE_GROUP=1: amplitudes sharing a colour pattern are made consecutive
+    # and summed in a register before the colour flows are updated (always on
+    # in chunked mode)
+    group = mode == "chunked" or os.environ.get("MG_LINE_GROUP", "0") == "1"
+    amp_order = [i for kind, i in program(plan, by_pattern=True) if kind == "amp"] if group else schedule(plan)
+    pid, psign, pats = colour_patterns(plan)
+    last_of = {}
+    for ai in amp_order:
+        last_of[pid[ai]] = ai
+
+    def emit_amp(ai):
         op, co = plan.amps[ai]
         if op[0] == "f":
             r, gq, c = cur(op[1]), cur(op[2]), cur(op[3])
@@ -303,6 +301,16 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             c = "g * g" if br in (0, 1) else "-g * g"
             expr = f"vvvv_amp<{br}, R>({nx}, {ny}, {nz}, {G}, {c})"
         L.append(f"  {{ const cx<R> a = {expr};")
+        if group:
+            L.append(f"    pacc = pacc {'+' if psign[ai] > 0 else '-'} a;")
+            if last_of[pid[ai]] == ai:
+                parts = []
+                for k, c in pats[pid[ai]]:
+                    parts.append(f"JAMP({k}) = JAMP({k}) {'+' if c > 0 else '-'} pacc;")
+                parts.append("pacc = cx<R>{R(0), R(0)};")
+                L.append("    " + " ".join(parts))
+            L.append("  }")
+            return
         parts = []
         for k, c in sorted(co.items()):
             if c == 1:
@@ -312,6 +320,110 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             else:
                 parts.append(f"JAMP({k}) = fma(R({c}), a, JAMP({k}));")
         L.append("    " + " ".join(parts) + " }")
+
+    if mode == "chunked":
+        main_L = L
+        chunk_size = CHUNK_AMPS
+        chunks, curc = [], []
+        for ai in amp_order:  # cut only at the end of a colour-pattern group
+            curc.append(ai)
+            if len(curc) >= chunk_size and last_of[pid[ai]] == ai:
+                chunks.append(curc)
+                curc = []
+        if curc:
+            chunks.append(curc)
+        # pass 1: where each current is produced and which later chunks read it
+        local_kinds = ("ext", "ubar", "v")
+        produced, readers = {}, {}
+        for j, ch in enumerate(chunks):
+            seen = set()
+
+            def visit(c, j=j, seen=seen):
+                if c in seen:
+                    return
+                seen.add(c)
+                if plan.ops[c][0] not in local_kinds and c in produced:
+                    readers.setdefault(c, set()).add(j)
+                    return
+                for d in current_deps(plan, c):
+                    visit(d)
+                if plan.ops[c][0] not in local_kinds:
+                    produced[c] = j
+            for ai in ch:
+                for d in amp_deps(plan, plan.amps[ai][0]):
+                    visit(d)
+        cross = {c for c in readers}
+        # store slots by interval colouring over chunk indices
+        intervals = sorted((produced[c], max(readers[c]), c) for c in cross)
+        slot_of, free_at = {}, []
+        for a0, a1, c in intervals:
+            for si, end in enumerate(free_at):
+                if end < a0:
+                    slot_of[c] = si
+                    free_at[si] = a1
+                    break
+            else:
+                slot_of[c] = len(free_at)
+                free_at.append(a1)
+        nstore = max(1, len(free_at))
+        chunk_funcs = []
+        for j, ch in enumerate(chunks):
+            L = []
+            emitted = {}
+            emitted_k = set()
+            imports = {c: slot_of[c] for c in cross if produced[c] < j and j in readers[c]}
+            L.append("template <typename R>")
+            L.append(f"__device__ static __noinline__ void chunk{j}(const R* __restrict__ ev, const int es, "
+                     "const int hel, const double* __restrict__ kp, V4<R>* __restrict__ W, "
+                     "cx<R>* __restrict__ jamp, const int js) {")
+            L.append("  const R g = R(kp[0]);")
+            L.append("  const R mt = R(kp[1]);")
+            for i in range(npar):
+                L.append(f"  const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
+            L.append("  cx<R> pacc = {R(0), R(0)};")
+            for ai in ch:
+                emit_amp(ai)
+            for c in sorted(cross):
+                if produced[c] == j:
+                    nm = emitted[c]
+                    conv = f"as_v4({nm})" if plan.ops[c][0] in ("row", "col") else nm
+                    L.append(f"  W[{slot_of[c]}] = {conv};")
+            L.append("}")
+            chunk_funcs.append(L)
+        L = main_L
+        # the driver replaces the straight-line body begun above
+        while not L[-1].startswith("  for (int c = 0;"):
+            L.pop()
+        L.append(f"  V4<R> W[{nstore}];  // currents passed between chunks")
+        for j in range(len(chunks)):
+            L.append(f"  chunk{j}<R>(ev, es, hel, kp, W, jamp, js);")
+        L.append("#undef JAMP")
+        L.append("#undef EV")
+        L.append("}")
+        # chunk functions are emitted before amplitudes(): move them in front
+        head = L.index("// one helicity: currents and amplitudes, diagram by diagram, into the colour flows")
+        body = L[head:]
+        del L[head:]
+        L.append("#define EV(k) ev[(k) * es]")
+        L.append("#define JAMP(k) jamp[(k) * js]")
+        for f in chunk_funcs:
+            L.extend(f)
+        L.append("#undef JAMP")
+        L.append("#undef EV")
+        L.append(f"static constexpr int NCHUNK = {len(chunks)};")
+        L.append(f"static constexpr int NSTORE = {nstore};")
+        L.extend(body)
+        L.append("")
+        L.extend(_colour_quadratic_looped(tag, ncol))
+        L.append(f"}};  // struct {tag}")
+        L.append("}  // namespace mg")
+        src = "\n".join(L) + "\n"
+        return src.replace(f"struct {tag} {{", _knum_table(tag, K) + f"\nstruct {tag} {{", 1)
+
+    if group:
+        L.append("  cx<R> pacc = {R(0), R(0)};")
+    for ai in amp_order:
+        emit_amp(ai)
     L.append("#undef JAMP")
     L.append("#undef EV")
     L.append("}")
@@ -540,123 +652,27 @@ def program(plan, by_pattern: bool = False) -> list[tuple[str, int]]:
     return seq
 
 
-def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
-    """Op table + interpreter-driven amplitudes() and a looped colour form."""
-    # amplitudes grouped by colour pattern (fewer colour-flow updates, a larger
-    # current store); MG_TABLE_GROUP=0 keeps the register-pressure order
-    by_pattern = os.environ.get("MG_TABLE_GROUP", "1") != "0"
-    seq = program(plan, by_pattern=by_pattern)
-    pid, psign, pats = colour_patterns(plan)
-    if not by_pattern:  # every amplitude its own group
-        pats = [tuple(sorted(co.items())) for op, co in plan.amps]
-        pid = list(range(len(plan.amps)))
-        psign = [1] * len(plan.amps)
-    amp_positions = [i for kind, i in seq if kind == "amp"]
-    last_of_pattern = {}
-    for ai in amp_positions:
-        last_of_pattern[pid[ai]] = ai
-    pat_jl = {}
-    gtt = plan.keys.get(("gtt",))
-    # inputs of every step, for liveness
-    def inputs(kind, i):
-        if kind == "cur":
-            return current_deps(plan, i)
-        return amp_deps(plan, plan.amps[i][0])
-    last = {}
-    for t, (kind, i) in enumerate(seq):
-        for d in inputs(kind, i):
-            last[d] = t
-    slot = {}
-    free = []
-    nstore = 0
-    ops = []
-    jl = []
-    ext_kinds = ("ext", "ubar", "v")
-    for t, (kind, i) in enumerate(seq):
-        if kind == "cur":
-            if free:
-                free.sort()
-                slot[i] = free.pop(0)
-            else:
-                slot[i] = nstore
-                nstore += 1
-            op = plan.ops[i]
-            k = op[0]
-            out = slot[i]
-            if k == "3":
-                ops.append([1, out, slot[op[1]], slot[op[2]], _mask_of(plan, op[1]), _mask_of(plan, op[2]),
-                            sl[f"cg{op[3]}"], 0])
-            elif k == "4":
-                ops.append([2, out, slot[op[1]], slot[op[2]], slot[op[3]], op[4], sl[f"cg{op[5]}"], 0])
-            elif k == "row":
-                ops.append([3, out, slot[op[1]], slot[op[2]], op[3], sl[f"cf{op[3]}"], 0, 0])
-            elif k == "col":
-                ops.append([4, out, slot[op[1]], slot[op[2]], op[3], sl[f"cf{full ^ op[3]}"], 0, 0])
-            elif k == "gtt":
-                ops.append([5, out, slot[plan.keys[("row", ())]], slot[plan.keys[("col", ())]], sl["cgtt"],
-                            0, 0, 0])
-            else:
-                assert k in ext_kinds
-        else:
-            op, co = plan.amps[i]
-            # amplitudes of one colour pattern are consecutive: accumulate them
-            # (with their sign relative to the pattern) and apply the pattern's
-            # flow list once, after the last of them (njl = 0 before that)
-            j0, nj = 0, 0
-            if last_of_pattern[pid[i]] == i:
-                j0 = len(jl)
-                for f, c in pats[pid[i]]:
-                    assert c in (1, -1), c
-                    jl.append((f << 1) | (1 if c < 0 else 0))
-                nj = len(jl) - j0
-            sg = 1 if psign[i] > 0 else 0
-            if op[0] == "f":
-                ops.append([6, slot[op[1]], slot[op[2]], slot[op[3]], 0, 0, j0, nj])
-            elif op[0] == "a3":
-                ops.append([7, slot[op[1]], slot[op[2]], _mask_of(plan, op[1]), _mask_of(plan, op[2]), slot[gtt],
-                            j0, nj])
-            else:
-                ops.append([8, slot[op[1]], slot[op[2]], slot[op[3]], op[4], slot[gtt], j0, nj])
-            ops[-1][0] |= (sg << 8)  # bit 8 of the type word: +1 (set) or -1 relative sign
-        for d in inputs(kind, i):
-            if last[d] == t and plan.ops[d][0] not in ext_kinds:
-                free.append(slot[d])
+def _knum_table(tag, K) -> str:
+    """Colour numerators as a device table: row i holds K_ii on the diagonal and
+    2 K_ij for j > i (the form is symmetric); the lower triangle is unused."""
+    ncol = len(K)
+    vals = []
+    for i in range(ncol):
+        for j in range(ncol):
+            vals.append(K[i][j] if j == i else (2 * K[i][j] if j > i else 0))
+    assert max(abs(v) for v in vals) < 32768
+    rows = [", ".join(str(v) for v in vals[i * ncol:(i + 1) * ncol]) for i in range(ncol)]
+    return (f"static __device__ const short {tag}_KNUM[{ncol * ncol}] = {{\n  " + ",\n  ".join(rows) + "};")
+
+
+def _colour_quadratic_looped(tag, ncol) -> list[str]:
+    """sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j) as a loop over the device
+    table (the straight-line form of a 120-flow process is too much code)."""
     L = []
-    L.append(f"static constexpr int NG = {n};")
-    chain = " : ".join(f"i == {i} ? {sl[f'k{i}']}" for i in range(n - 1)) + f" : {sl[f'k{n - 1}']}"
-    L.append("// slab offset of gluon i's incoming momentum")
-    L.append(f"__host__ __device__ static constexpr int koff(int i) {{ return {chain}; }}")
-    L.append(f"static constexpr int PT = {sl['pt']};")
-    L.append(f"static constexpr int PTB = {sl['ptb']};")
-    L.append(f"static constexpr int NOPS = {len(ops)};")
-    L.append(f"static constexpr int NSTORE = {nstore};")
-    L.append(f"static constexpr int NJL = {len(jl)};")
-    L.append("// per-helicity program: externals into the store, then the op table")
-    L.append("template <typename R>")
-    L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
-    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp,")
-    L.append("                                           const int js) {")
-    L.append("#define EV(k) ev[(k) * es]")
-    L.append("  const R g = R(kp[0]);")
-    L.append("  const R mt = R(kp[1]);")
-    for i in range(npar):
-        L.append(f"  const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
-    L.append(f"  V4<R> W[{nstore}];")
-    gl_slots = [0, 1] + list(range(4, n + 2))
-    for i in range(n):
-        cid = plan.keys[("g", ("L", i))]
-        L.extend(_ext_gluon_lines(f"W[{slot[cid]}]", i, gl_slots[i], sl, declare=False))
-    L.extend(_ext_top_lines(f"W[{slot[plan.keys[('row', ())]]}]", "ubar", sl, declare=False, wrap=True))
-    L.extend(_ext_top_lines(f"W[{slot[plan.keys[('col', ())]]}]", "v", sl, declare=False, wrap=True))
-    L.append(f"  for (int c = 0; c < {ncol}; c++) jamp[c * js] = cx<R>{{R(0), R(0)}};")
-    L.append(f"  run_program<{tag}, R>({tag}_OPS, NOPS, {tag}_JL, ev, es, g, mt, W, jamp, js);")
-    L.append("#undef EV")
-    L.append("}")
-    L.append("// sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j), KNUM from the table knum")
+    L.append("// sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j); |M|^2 colour sum = result / CDEN")
     L.append("template <typename R>")
     L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
     L.append(f"  const short* __restrict__ knum = {tag}_KNUM;")
-    L.append("  // symmetric: diagonal once, off-diagonal pairs j > i twice (knum holds 2 K_ij there)")
     L.append("  R acc = R(0);")
     L.append("#pragma unroll 1")
     L.append(f"  for (int i = 0; i < {ncol}; i++) {{")
@@ -674,21 +690,8 @@ def _table_sections(plan, tag, n, npar, ncol, sl, slots, full, K) -> list[str]:
     L.append("  }")
     L.append("  return acc;")
     L.append("}")
-    # data tables (outside the struct: emitted after it by the caller)
-    table_src = []
-    table_src.append(f"static __device__ const int4 {tag}_OPS[{2 * len(ops)}] = {{")
-    for o in ops:
-        table_src.append(f"  {{{o[0]}, {o[1]}, {o[2]}, {o[3]}}}, {{{o[4]}, {o[5]}, {o[6]}, {o[7]}}},")
-    table_src.append("};")
-    table_src.append(f"static __device__ const short {tag}_JL[{len(jl)}] = {{{', '.join(map(str, jl))}}};")
-    # upper triangle doubled (the symmetric loop reads K_ii and 2 K_ij, j > i); |2 K| <= 8192 fits a short
-    KS = [[K[i][j] if i == j else (2 * K[i][j] if j > i else 0) for j in range(ncol)] for i in range(ncol)]
-    table_src.append(f"static __device__ const short {tag}_KNUM[{ncol * ncol}] = {{{_fmt_knum(KS)}}};")
-    _TABLES[tag] = table_src
     return L
 
-
-_TABLES: dict = {}
 
 
 def _mask_of(plan, cid) -> int:
@@ -773,8 +776,12 @@ def emit_eemumu(tag: str) -> str:
     return "\n".join(L) + "\n"
 
 
-# processes evaluated by the table interpreter (straight-line code too large to compile)
-TABLE_MODE = {"ggttggg"}
+# processes emitted as straight-line code cut into separately compiled chunk
+# functions of about CHUNK_AMPS amplitudes (one straight-line function of this
+# size does not compile in reasonable time); currents that cross a chunk
+# boundary are passed through a per-thread store
+CHUNKED = {"ggttggg"}
+CHUNK_AMPS = int(os.environ.get("MG_CHUNK_AMPS", "40"))
 
 
 def emit(proc: str) -> tuple[str, str]:
@@ -782,12 +789,7 @@ def emit(proc: str) -> tuple[str, str]:
     tag, n = PROCESSES[proc]
     if n == 0:
         return tag, emit_eemumu(tag)
-    if tag in TABLE_MODE:
-        src = emit_gg(n, tag, mode="table")
-        tables = "\n".join(_TABLES.pop(tag))
-        src = src.replace('#include "mg_vertices.cuh"', '#include "mg_vertices.cuh"\n#include "mg_interp.cuh"')
-        return tag, src.replace(f"struct {tag} {{", f"{tables}\nstruct {tag} {{", 1)
-    return tag, emit_gg(n, tag)
+    return tag, emit_gg(n, tag, mode="chunked" if tag in CHUNKED else "straight")
 
 
 # threads per CTA: FP64 path / mixed path (shared-memory slab sizes differ)
@@ -806,48 +808,55 @@ THREADS = {
 TENSOR_CORE_COLOUR = {"ggttg", "ggttgg"}
 
 
-def emit_kernels_tu(proc: str) -> tuple[str, str]:
-    """Translation unit instantiating the kernels of one process."""
-    tag, _ = PROCESSES[proc]
+# processes whose vertex routines are called rather than inlined, per
+# precision: the straight-line helicity program then shrinks to a sequence of
+# calls to a few small routines that stay in the instruction cache.  Measured:
+# faster for the FP32 path of the larger processes, whose inlined program
+# streams from L2 on every helicity; the FP64 path of gg -> t t~ g g (bound by
+# the FP64 pipe) and the smaller processes keep the inlined code
+VERTEX_CALLS = {"f32": {"ggttgg", "ggttggg"}, "f64": {"ggttggg"}}
+
+
+def emit_tu(proc: str, prec: str) -> tuple[str, str]:
+    """Translation unit instantiating the kernels of one process in one
+    precision ("f64": FP64 |M|^2, helicity scan, FP64 helicity/colour choice,
+    the paper's mixed mode, and the process descriptor; "f32": the mixed
+    |M|^2 and the mixed helicity/colour choice)."""
+    tag, n = PROCESSES[proc]
     nt64, nt32 = THREADS[tag]
+    calls = "#define MG_VERTEX __noinline__\n" if tag in VERTEX_CALLS[prec] else ""
+    head = f"// generated by paper_2303_18244_gb300.generator: {prec} kernels of '{proc}'\n{calls}"
     tc = tag in TENSOR_CORE_COLOUR
-    mixed = f"launch_sigma_tc<{tag}>(a)" if tc else f"launch_sigma<{tag}, float, {nt32}>(a)"
-    tck = f"tc::pad16({tag}::NCOL)" if tc else "0"
-    src = f"""// generated by paper_2303_18244_gb300.generator: kernels of '{proc}'
-#include "../mg_kernels.cuh"
-#include "../mg_colour_tc.cuh"
+    if prec == "f32":
+        mixed = f"launch_sigma_tc<{tag}>(a)" if tc else f"launch_sigma<{tag}, float, {nt32}>(a)"
+        inc = '#include "../mg_colour_tc.cuh"\n' if tc else ""
+        src = f"""{head}#include "../mg_kernels.cuh"
+{inc}#include "{tag}.cuh"
+
+namespace mg {{
+int sigma_{tag}_mixed(const LaunchArgs& a) {{ return {mixed}; }}
+int select_{tag}_mixed(const LaunchArgs& a) {{ return launch_select<{tag}, float, {nt32}>(a); }}
+}}  // namespace mg
+"""
+        return tag, src
+    ncol = 1 if n == 0 else math.factorial(n)
+    tck = ((ncol + 15) // 16) * 16 if tc else 0
+    src = f"""{head}#include "../mg_kernels.cuh"
 #include "{tag}.cuh"
 
 namespace mg {{
 static int sigma_fp64(const LaunchArgs& a) {{ return launch_sigma<{tag}, double, {nt64}>(a); }}
-static int sigma_mixed(const LaunchArgs& a) {{ return {mixed}; }}
 static int helicities(const LaunchArgs& a) {{ return launch_helicities<{tag}, {nt64}>(a); }}
-int select_{tag}_fp64(const LaunchArgs& a);
+static int select_fp64(const LaunchArgs& a) {{ return launch_select<{tag}, double, {nt64}>(a); }}
+static int paper(const LaunchArgs& a) {{ return launch_sigma_paper<{tag}, {nt64}>(a); }}
+int sigma_{tag}_mixed(const LaunchArgs& a);
 int select_{tag}_mixed(const LaunchArgs& a);
-int paper_{tag}(const LaunchArgs& a);
+static_assert({tag}::NCOL == {ncol}, "colour-flow count");
 static const ProcDesc desc = {{"{proc}", "{tag}", {tag}::NPAR, {tag}::NHEL, {tag}::NCOL, {tag}::NDIAG,
                               {tag}::NAMP, {tag}::IDEN, {tag}::CDEN, {tag}::KNUM,
-                              sigma_fp64, sigma_mixed, helicities, {tck},
-                              select_{tag}_fp64, select_{tag}_mixed, paper_{tag}}};
+                              sigma_fp64, sigma_{tag}_mixed, helicities, {tck},
+                              select_fp64, select_{tag}_mixed, paper}};
 const ProcDesc* proc_{tag}() {{ return &desc; }}
-}}  // namespace mg
-"""
-    return tag, src
-
-
-def emit_select_tu(proc: str) -> tuple[str, str]:
-    """Translation unit of the helicity/colour-choice kernels and of the
-    paper-style mixed kernel (compiled in parallel with the main kernels)."""
-    tag, _ = PROCESSES[proc]
-    nt64, nt32 = THREADS[tag]
-    src = f"""// generated by paper_2303_18244_gb300.generator: helicity/colour choice kernels of '{proc}'
-#include "../mg_kernels.cuh"
-#include "{tag}.cuh"
-
-namespace mg {{
-int select_{tag}_fp64(const LaunchArgs& a) {{ return launch_select<{tag}, double, {nt64}>(a); }}
-int select_{tag}_mixed(const LaunchArgs& a) {{ return launch_select<{tag}, float, {nt32}>(a); }}
-int paper_{tag}(const LaunchArgs& a) {{ return launch_sigma_paper<{tag}, {nt64}>(a); }}
 }}  // namespace mg
 """
     return tag, src

@@ -28,7 +28,7 @@ MG_PHOTON_ONLY = 2
 EXPORTS = (
     "mg_params_default", "mg_process_create", "mg_process_destroy", "mg_process_info",
     "mg_good_helicities", "mg_sigma", "mg_sigma_host", "mg_process_status", "mg_sigma_helicities",
-    "mg_good_helicities_static", "mg_rambo", "mg_sigma_select",
+    "mg_good_helicities_static", "mg_rambo", "mg_sigma_select", "mg_unweight",
     "mg_server_cfg_default", "mg_server_create", "mg_server_submit", "mg_server_poll",
     "mg_server_destroy", "mg_strerror",
     # include/mg_diag.h
@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         L.mg_good_helicities_static.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
         L.mg_sigma.argtypes = [vp, vp, i64, vp, vp]
         L.mg_rambo.argtypes = [vp, ctypes.c_double, ctypes.c_uint64, i64, i64, vp, vp]
+        L.mg_unweight.argtypes = [vp, vp, i64, ctypes.c_double, vp, vp, vp]
         L.mg_sigma_select.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
         L.mg_sigma_host.argtypes = [vp, vp, i64, vp, vp]
         L.mg_process_status.argtypes = [vp]
@@ -214,6 +215,20 @@ def rambo(h: Process, sqrt_s: float, seed: int, first_event: int, momenta_dev, s
     nevt = momenta_dev.shape[0]
     _check(lib().mg_rambo(h.handle, sqrt_s, seed, first_event, nevt, _dev_check(momenta_dev),
                           _stream_ptr(stream)), "mg_rambo")
+
+
+def unweight(w_dev, r_dev, w_max: float, idx_out_dev, n_acc_dev, stream=None):
+    """mg_unweight: kept indices (r * w_max < w) in increasing order into
+    idx_out_dev (int64 [n]); their number into n_acc_dev (int64 [1]). All CUDA."""
+    import torch
+    n = w_dev.shape[0]
+    for t in (idx_out_dev, n_acc_dev):
+        if not (t.is_cuda and t.dtype == torch.int64 and t.is_contiguous()):
+            raise TypeError("expected contiguous int64 CUDA tensors for the outputs")
+    if r_dev.shape[0] != n or idx_out_dev.shape[0] < n:
+        raise ValueError("w, r and idx_out must hold n events")
+    _check(lib().mg_unweight(_dev_check(w_dev), _dev_check(r_dev), n, w_max, idx_out_dev.data_ptr(),
+                             n_acc_dev.data_ptr(), _stream_ptr(stream)), "mg_unweight")
 
 
 def sigma_select(h: Process, momenta_dev, rnd_dev, me_out_dev, hel_out_dev, col_out_dev, colw_out_dev=None,

@@ -1,0 +1,92 @@
+"""Device hit-or-miss unweighting (mg_unweight) against the oracle's
+definition: the kept index list must be identical (integer work: bit-exact)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2303_18244_gb300 import mg  # noqa: E402
+from paper_2303_18244_gb300.inputs import process_momenta, uniforms  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TILE = 2048  # events per tile of the device kernels
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _run(w, r, w_max):
+    n = w.shape[0]
+    wd = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    rd = torch.from_numpy(np.ascontiguousarray(r)).cuda()
+    idx = torch.full((max(n, 1),), -7, dtype=torch.int64, device="cuda")
+    cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    mg.unweight(wd, rd, w_max, idx, cnt)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    return idx.cpu().numpy()[:k], k, idx.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1, 31, 257, TILE - 1, TILE, TILE + 1, 5 * TILE + 333, 1 << 20])
+def test_matches_oracle(n):
+    u = uniforms(21, 0, n, 1)[:, 0, :]
+    w = 4.0 * u[:, 0] ** 2
+    r = u[:, 1]
+    got, k, raw = _run(w, r, 1.5)
+    want = O.unweight(w, r, 1.5)
+    assert k == want.size
+    assert np.array_equal(got, want)
+    assert np.all(raw[k:n] == -7)  # nothing written past the kept events
+
+
+def test_all_and_none_kept():
+    n = 3 * TILE + 5
+    u = uniforms(22, 0, n, 1)[:, 0, 0]
+    got, k, _ = _run(np.full(n, 2.0), u, 1.0)
+    assert k == n and np.array_equal(got, np.arange(n))
+    got, k, _ = _run(np.zeros(n), u, 1.0)
+    assert k == 0
+
+
+def test_empty_and_bad_args():
+    cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    ei = torch.empty(0, dtype=torch.int64, device="cuda")
+    mg.unweight(e, e, 1.0, ei, cnt)
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == 0
+    w = torch.ones(10, dtype=torch.float64, device="cuda")
+    idx = torch.empty(10, dtype=torch.int64, device="cuda")
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(mg.MGError):
+            mg.unweight(w, w, bad, idx, cnt)
+
+
+def test_unweighted_events_from_matrix_elements():
+    # the full chain on the device: phase space, |M|^2, unweighting against
+    # the largest weight of the batch; the kept set equals the oracle's on
+    # the same device weights
+    proc, sqrts, n = "g g > t t~", 1000.0, 200000
+    h = mg.Process(proc)
+    mg.good_helicities(h, torch.from_numpy(process_momenta(proc, sqrts, 1024, 1002)).cuda())
+    mom = torch.empty((n, 4, 4), dtype=torch.float64, device="cuda")
+    mg.rambo(h, sqrts, 2, 0, mom)
+    me = torch.empty(n, dtype=torch.float64, device="cuda")
+    mg.sigma(h, mom, me)
+    r = torch.from_numpy(uniforms(23, 0, n, 1)[:, 0, 0].copy()).cuda()
+    w_max = float(me.max().item())
+    idx = torch.empty(n, dtype=torch.int64, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    mg.unweight(me, r, w_max, idx, cnt)
+    torch.cuda.synchronize()
+    k = int(cnt.item())
+    want = O.unweight(me.cpu().numpy(), r.cpu().numpy(), w_max)
+    assert np.array_equal(idx[:k].cpu().numpy(), want)
+    # efficiency <w>/w_max within 5 sigma
+    p = me.cpu().numpy() / w_max
+    assert abs(k - p.sum()) < 5 * np.sqrt((p * (1 - p)).sum())
