@@ -9,8 +9,9 @@ with the good-helicity set-up (A0) done once before timing.  The headline
 value is the mixed-precision path; the FP64 path on the same events, the
 mixed-vs-FP64 accuracy, an end-to-end number through host buffers, the
 roofline of the dominant kernel and the FP64 CPU oracle's throughput on a
-bounded sample are reported beside it.  --serve adds the continuous-batching
-request loop (Poisson arrivals, four processes) with p50/p99 latency.
+bounded sample are reported beside it, with a short run (120 requests, mixed)
+of the continuous-batching request loop (Poisson arrivals, four processes,
+p50/p99 latency); --serve runs it with 2000 mixed and 200 FP64 requests.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 
@@ -44,9 +45,15 @@ WORKLOADS = {
     "ggtt": ("g g > t t~", 1000.0, 2, 524288),
     "ggttgg": ("g g > t t~ g g", 1500.0, 3, 524288),
     "ggttggg": ("g g > t t~ g g g", 2000.0, 4, 65536),
+    "uutt": ("u u~ > t t~", 1000.0, 7, 524288),
 }
 METRIC = "gg→tt̄gg MEs/s on 1 GB300, FP64 vs mixed (≤1e-5 rel err); serve p50/p99 ms"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the mixed
+# kernel from one ncu capture of the current kernel on a small case: workload
+# -> (events captured, bytes); scaled to a launch by its events (the traffic
+# is per event: momenta in, |M|^2 out).  Set to None when the kernel changes.
+NCU_TRAFFIC = {"ggttgg": None}
 
 SERVE_PROCS = {  # process -> sqrt(s)
     "e+ e- > mu+ mu-": 500.0,
@@ -179,7 +186,7 @@ def main():
     ap.add_argument("--nevt", type=int, default=None)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--serve", action="store_true",
-                    help="full serving benchmark (400 requests, mixed and FP64) instead of the short mixed one")
+                    help="full serving benchmark (2000 mixed and 200 FP64 requests) instead of the short mixed one")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -282,6 +289,9 @@ def main():
     peak64 = mg.diag_fma_peak(1) / 1e3
     achieved64 = flops_evt * nevt / (t_64 * 1e-3) / 1e12
 
+    cap = NCU_TRAFFIC.get(args.proc)
+    traffic = None if cap is None else cap[1] * nevt / cap[0]
+
     res = {
         "metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mix / args.steps, "higher_is_better": True,
@@ -300,7 +310,7 @@ def main():
         "e2e": {"value": world * nevt / (e2e_t * 1e-3), "unit": "MEs/s",
                 "h2d_bytes_per_step": int(p.nbytes), "d2h_bytes_per_step": int(nevt * 8)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                     "frac": achieved / peak32, "traffic": None,
+                     "frac": achieved / peak32, "traffic": traffic,
                      "kernel": f"sigma kernel of {args.proc}, mixed",
                      "flops_per_event": flops_evt,
                      "peak_source": "measured FP32 FMA loop (mg_diag), burst"},
@@ -312,9 +322,9 @@ def main():
         res["cpu_baseline"] = {"value": v, "unit": "MEs/s", "cores": cores, "kind": "oracle",
                                "sample": f"{n} events of the workload ({dt:.1f} s wall)"}
     if not args.no_serve and args.proc == "ggttgg":
-        nreq = args.serve_requests or (400 if args.serve else 120)
-        precs = ("mixed", "fp64") if args.serve else ("mixed",)
-        res["serve"] = serve_bench(nreq, precs, mg, process_momenta)
+        nreq = args.serve_requests or (2000 if args.serve else 120)
+        plan = {"mixed": nreq, "fp64": max(1, nreq // 10)} if args.serve else {"mixed": nreq}
+        res["serve"] = serve_bench(plan, mg, process_momenta)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
@@ -322,15 +332,17 @@ def main():
     return 0
 
 
-def serve_bench(nreq, precs, mg, process_momenta):
+def serve_bench(plan, mg, process_momenta):
     """Poisson arrivals (mean gap 2 ms) of requests drawn uniformly from four
     processes, log-uniform 256..65536 events each (Philox seed 5 drives the
-    choices), served by the continuous-batching loop; p50/p99 latency."""
+    choices), served by the continuous-batching loop; p50/p99 latency.
+    plan: precision name -> number of requests."""
     from paper_2303_18244_gb300.inputs import uniforms
     out = {}
     for prec_name, prec in (("mixed", mg.MG_MIXED), ("fp64", mg.MG_FP64)):
-        if prec_name not in precs:
+        if prec_name not in plan:
             continue
+        nreq = plan[prec_name]
         handles = {p: mg.Process(p, precision=prec) for p in SERVE_PROCS}
         for p, hh in handles.items():
             calib = process_momenta(p, SERVE_PROCS[p], 1024, 1005)

@@ -31,6 +31,7 @@ PROCS = {
     "g g > t t~ g": 2,
     "g g > t t~ g g": 3,
     "g g > t t~ g g g": 4,
+    "u u~ > t t~": 5,
 }
 
 
@@ -128,7 +129,7 @@ def me(proc: str, momenta: np.ndarray, params: Params | None = None,
     out = np.empty(nevt, dtype=np.float64)
     pa = params.array()
     L = lib_ext() if extended else lib()
-    if proc != "e+ e- > mu+ mu-":
+    if proc.startswith("g g"):
         colour_matrix(pid + 1)  # fill the colour-matrix cache once, outside the pool
     threads = threads or os.cpu_count() or 1
     threads = max(1, min(threads, nevt))

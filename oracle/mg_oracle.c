@@ -18,6 +18,8 @@
  *
  *   - e+ e- -> mu+ mu-: the two s-channel diagrams (photon, Z) written out
  *     with explicit 4x4 Dirac matrices;
+ *   - u u~ -> t t~: the s-channel gluon diagram with explicit Dirac matrices
+ *     and an explicit sum over every colour index;
  *   - g g -> t t~ + (n-2) g: colour decomposition on one quark line,
  *       M = sum_{sigma in S_n} (T^{a_sigma1} ... T^{a_sigman})_{i_t j_tbar} A(sigma),
  *     partial amplitudes A(sigma) from colour-ordered Berends-Giele recursion
@@ -67,7 +69,7 @@ static const real PI_R = 3.14159265358979323846264338327950288L;
 #define MGO_ERR_ARG (-1)
 #define MGO_ERR_NOMEM (-2)
 
-enum { MGO_EEMUMU = 0, MGO_GGTT = 1, MGO_GGTTG = 2, MGO_GGTTGG = 3, MGO_GGTTGGG = 4 };
+enum { MGO_EEMUMU = 0, MGO_GGTT = 1, MGO_GGTTG = 2, MGO_GGTTGG = 3, MGO_GGTTGGG = 4, MGO_UUTT = 5 };
 
 #define MAXG 5     /* at most 5 gluons */
 #define MAXPERM 120
@@ -842,6 +844,56 @@ static real me_eemumu(const oparams* o, const real* mom) {
   return sum / 4.0;
 }
 
+/* u(p1) u~(p2) -> t(p3) t~(p4): the one s-channel gluon diagram,
+ *   M = [vbar(p2) (i g gamma^mu T^a) u(p1)] (-i g_{mu nu} / s) [ubar(p3) (i g gamma^nu T^a) v(p4)],
+ * with every colour index summed explicitly over the Gell-Mann generators
+ * (colour factor sum_{ijkl} |sum_a T^a_{ji} T^a_{kl}|^2) and every spin state
+ * summed with explicit Dirac-representation spinors.  IDEN = 4 spins x 9
+ * colours. */
+static real me_uutt(const oparams* o, const real* mom) {
+  const real* p1 = mom;
+  const real* p2 = mom + 4;
+  const real* p3 = mom + 8;
+  const real* p4 = mom + 12;
+  const real g = sqrt(4.0 * PI_R * o->alpha_s);
+  real ptot[4];
+  for (int mu = 0; mu < 4; mu++) ptot[mu] = p1[mu] + p2[mu];
+  const real s = dot_rr(ptot, ptot);
+  real colour = 0.0;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++)
+      for (int k = 0; k < 3; k++)
+        for (int l = 0; l < 3; l++) {
+          cplx c = 0.0;
+          for (int a = 0; a < 8; a++) c += TGEN[a][j][i] * TGEN[a][k][l];
+          colour += creal(c * conj(c));
+        }
+  real sum = 0.0;
+  for (int s1 = 0; s1 < 2; s1++)
+    for (int s2 = 0; s2 < 2; s2++)
+      for (int s3 = 0; s3 < 2; s3++)
+        for (int s4 = 0; s4 < 2; s4++) {
+          cplx u1[4], v2[4], vb2[4], u3[4], ub3[4], v4[4];
+          spinor_u(p1, 0.0, s1, u1);
+          spinor_v(p2, 0.0, s2, v2);
+          dirac_bar(v2, vb2);
+          spinor_u(p3, o->mt, s3, u3);
+          dirac_bar(u3, ub3);
+          spinor_v(p4, o->mt, s4, v4);
+          cplx jl[4], jh[4];
+          for (int mu = 0; mu < 4; mu++) {
+            cplx t[4];
+            matcol((const cplx(*)[4])GAM[mu], u1, t);
+            jl[mu] = I * g * rowcol(vb2, t);
+            matcol((const cplx(*)[4])GAM[mu], v4, t);
+            jh[mu] = I * g * rowcol(ub3, t);
+          }
+          const cplx m = dot_cc(jl, jh) * (-I / s);
+          sum += creal(m * conj(m));
+        }
+  return sum * colour / 36.0;
+}
+
 /* g(p1) g(p2) -> t(p3) t~(p4) g(p5) ... : n gluons in total.
  * flow_w (may be NULL): sum over spin states of |A(sigma)|^2 per ordering. */
 static real me_ggtt_ng_w(const oparams* o, int n, const real* mom, real* flow_w);
@@ -916,7 +968,7 @@ static int proc_gluons(int proc) {
 }
 
 int mgo_npar(int proc) {
-  if (proc == MGO_EEMUMU) return 4;
+  if (proc == MGO_EEMUMU || proc == MGO_UUTT) return 4;
   const int n = proc_gluons(proc);
   return n ? n + 2 : MGO_ERR_ARG;
 }
@@ -946,11 +998,13 @@ int mgo_me(int proc, const double* params, const double* mom, int64_t nevt, doub
   unpack_params(params, &o);
   const int npar = mgo_npar(proc);
   if (npar < 0 || nevt < 0) return MGO_ERR_ARG;
-  if (proc != MGO_EEMUMU && !colour_matrix(proc_gluons(proc))) return MGO_ERR_NOMEM;
+  if (proc_gluons(proc) && !colour_matrix(proc_gluons(proc))) return MGO_ERR_NOMEM;
   for (int64_t e = 0; e < nevt; e++) {
     real p[4 * (MAXG + 2)];
     for (int i = 0; i < npar * 4; i++) p[i] = mom[(size_t)e * npar * 4 + i];
-    me[e] = (double)((proc == MGO_EEMUMU) ? me_eemumu(&o, p) : me_ggtt_ng(&o, proc_gluons(proc), p));
+    me[e] = (double)((proc == MGO_EEMUMU) ? me_eemumu(&o, p)
+                     : (proc == MGO_UUTT) ? me_uutt(&o, p)
+                                          : me_ggtt_ng(&o, proc_gluons(proc), p));
   }
   return MGO_OK;
 }

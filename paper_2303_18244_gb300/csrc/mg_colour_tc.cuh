@@ -104,22 +104,34 @@ __host__ __device__ constexpr uint32_t tile_off(int row, int k, int K) {
 
 // Shared-memory layout of the tensor-core kernel.  The momenta tile is dead
 // once the per-event set-up has run, so the operand tiles reuse its space.
+// With MG_TC_ALIAS the colour-flow accumulators share that space too (each
+// thread moves its flows into registers before the operand tiles are
+// written), which leaves the constant B tile and the slab as the only other
+// regions.
+#ifndef MG_TC_ALIAS
+#define MG_TC_ALIAS 0
+#endif
 template <class P, int NT>
 struct LayoutTC {
+  static constexpr bool alias = MG_TC_ALIAS != 0;
   static constexpr int K = tc::pad16(P::NCOL);
   static constexpr int N = tc::pad16(P::NCOL);
+  static constexpr size_t r128(size_t b) { return ((b + 127) / 128) * 128; }
   static constexpr size_t a_tile = size_t(NT) * K * 2;  // FP16 [NT][K]
   static constexpr size_t b_tile = size_t(N) * K * 2;   // FP16 [N][K]
   static constexpr size_t bar_bytes = 128;               // TMA bar, MMA bar, TMEM address
   static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
-  static constexpr size_t ops_bytes = 4 * a_tile + b_tile;
-  static constexpr size_t region_bytes = stage_bytes > ops_bytes ? stage_bytes : ops_bytes;
-  static constexpr size_t region_off = bar_bytes;  // no-swizzle tiles need 16-byte alignment only
-  static constexpr size_t slab_off = region_off + ((region_bytes + 127) / 128) * 128;
-  static constexpr size_t slab_bytes = size_t(NT) * P::NSLOT * sizeof(float);
-  static constexpr size_t jamp_off = slab_off + ((slab_bytes + 127) / 128) * 128;
   static constexpr size_t jamp_bytes = size_t(NT) * P::NCOL * sizeof(cx<float>);
-  static constexpr size_t base_bytes = jamp_off + ((jamp_bytes + 127) / 128) * 128;
+  static constexpr size_t slab_bytes = size_t(NT) * slab_slots<P, float>() * sizeof(float);
+  static constexpr size_t ops_bytes = 4 * a_tile + (alias ? 0 : b_tile);
+  static constexpr size_t region_bytes = stage_bytes > ops_bytes
+                                             ? (alias && jamp_bytes > stage_bytes ? jamp_bytes : stage_bytes)
+                                             : (alias && jamp_bytes > ops_bytes ? jamp_bytes : ops_bytes);
+  static constexpr size_t region_off = bar_bytes;  // no-swizzle tiles need 16-byte alignment only
+  static constexpr size_t b_off = alias ? region_off + r128(region_bytes) : region_off + 4 * a_tile;
+  static constexpr size_t slab_off = alias ? b_off + r128(b_tile) : region_off + r128(region_bytes);
+  static constexpr size_t jamp_off = alias ? region_off : slab_off + r128(slab_bytes);
+  static constexpr size_t base_bytes = alias ? slab_off + r128(slab_bytes) : jamp_off + r128(jamp_bytes);
   static constexpr uint32_t tmem_cols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
 };
 
@@ -155,7 +167,7 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
 
   // colour matrix tile (constant), operand tiles, accumulators
   unsigned char* atile = region;                    // 4 tiles: re_hi, re_lo, im_hi, im_lo
-  unsigned char* btile = region + 4 * LY::a_tile;
+  unsigned char* btile = smem + LY::b_off;
   for (int i = tid; i < (int)(LY::b_tile / 16); i += NT)
     reinterpret_cast<uint4*>(btile)[i] = __ldg(ctile + i);
   if (tid == 0) {
@@ -185,17 +197,28 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
   for (int ih = 0; ih < nhel && ok; ih++) {
     const int h = __ldg(hels + ih);
     P::template amplitudes<float>(slab + tid, NT, h, kp.v, jamp, NT);
+    // the event's flows into registers (their space may hold the operand tiles)
+    float fr[P::NCOL], fi[P::NCOL];
+#pragma unroll
+    for (int k = 0; k < P::NCOL; k++) {
+      fr[k] = jamp[k * NT].re;
+      fi[k] = jamp[k * NT].im;
+    }
+    if constexpr (LY::alias) __syncthreads();
     // per-event power-of-two scale, FP16 hi/lo split into the operand tiles
     float mx = 0.f;
-    for (int k = 0; k < P::NCOL; k++) mx = fmaxf(mx, fmaxf(fabsf(jamp[k * NT].re), fabsf(jamp[k * NT].im)));
+#pragma unroll
+    for (int k = 0; k < P::NCOL; k++) mx = fmaxf(mx, fmaxf(fabsf(fr[k]), fabsf(fi[k])));
     const int ex = mx > 0.f ? ((int)((__float_as_uint(mx) >> 23) & 0xff) - 127) : 0;
     const float s = __uint_as_float((uint32_t)(127 - ex) << 23);  // 2^-ex
+#pragma unroll
     for (int j = 0; j < K / 8; j++) {
       __align__(16) __half hr[8], lr[8], hi_[8], li[8];
+#pragma unroll
       for (int q = 0; q < 8; q++) {
         const int k = 8 * j + q;
-        const float xr = k < P::NCOL ? s * jamp[k * NT].re : 0.f;
-        const float xi = k < P::NCOL ? s * jamp[k * NT].im : 0.f;
+        const float xr = k < P::NCOL ? s * fr[k < P::NCOL ? k : 0] : 0.f;
+        const float xi = k < P::NCOL ? s * fi[k < P::NCOL ? k : 0] : 0.f;
         hr[q] = __float2half_rn(xr);
         lr[q] = __float2half_rn(xr - __half2float(hr[q]));
         hi_[q] = __float2half_rn(xi);
@@ -242,8 +265,8 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
 #pragma unroll
       for (int q = 0; q < 16; q++) {
         if (c + q < P::NCOL) {
-          dsum = fmaf(jamp[(c + q) * NT].re, dr[q], dsum);
-          dsum = fmaf(jamp[(c + q) * NT].im, di[q], dsum);
+          dsum = fmaf(fr[c + q < P::NCOL ? c + q : 0], dr[q], dsum);
+          dsum = fmaf(fi[c + q < P::NCOL ? c + q : 0], di[q], dsum);
         }
       }
     }
@@ -292,6 +315,193 @@ inline bool colour_tile_host(const int* knum, int ncol, unsigned short* out /* [
       out[tc::tile_off(n, k, K) / 2] = (unsigned short)b;
     }
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// Two-phase mixed path for processes whose colour operands do not fit in
+// shared memory beside the per-event state (120 flows): flows_kernel writes
+// the FP32 flows of every (good helicity, event) row to a workspace in HBM;
+// colour_rows_tc_kernel contracts them with the colour matrix on the tensor
+// cores, batched over events x helicities, and sums the helicities per event.
+// ---------------------------------------------------------------------------
+template <class P>
+struct LayoutRows {
+  static constexpr int K = tc::pad16(P::NCOL);
+  static constexpr int N = tc::pad16(P::NCOL);
+  static constexpr size_t a_tile = size_t(128) * K * 2;  // FP16 [128][K]
+  static constexpr size_t b_tile = size_t(N) * K * 2;    // FP16 [N][K]
+  static constexpr size_t a_off = 128;                    // MMA bar, TMEM address
+  static constexpr size_t b_off = a_off + 4 * a_tile;
+  static constexpr size_t base_bytes = b_off + b_tile;
+  static constexpr uint32_t tmem_cols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
+};
+
+// One CTA per 128 rows of events (TMEM lane = event).  Per helicity of the
+// slice: the rows' flows from J (rows past nevt read as zero), a per-row
+// power-of-two scale, FP16 hi/lo operand tiles, D = A K in TMEM for Re and
+// Im, then sum_k J_k D_k with the FP32 flows; helicities summed in FP64 into
+// me: a later slice continues the running sum stored by the one before, so
+// the helicities are added in the same order however they are sliced; the
+// last slice normalises.
+template <class P>
+__global__ void __launch_bounds__(128, 1)
+    colour_rows_tc_kernel(const float2* __restrict__ J, long long ldj, long long nevt, double* __restrict__ me,
+                          int nhel, int first, int last, const uint4* __restrict__ ctile,
+                          unsigned* __restrict__ status) {
+  using LY = LayoutRows<P>;
+  constexpr int NT = 128, K = LY::K, N = LY::N;
+  static_assert(2 * N <= 256, "two accumulators of N columns");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* mma_bar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+  unsigned char* atile = smem + LY::a_off;
+  unsigned char* btile = smem + LY::b_off;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const long long e = (long long)blockIdx.x * NT + tid;
+  const bool valid = e < nevt;
+
+  for (int i = tid; i < (int)(LY::b_tile / 16); i += NT) reinterpret_cast<uint4*>(btile)[i] = __ldg(ctile + i);
+  if (tid == 0) {
+    mbar_init(mma_bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, LY::tmem_cols);
+    tc::tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  constexpr uint32_t idesc = tc::idesc_f16(128, N);
+  const uint32_t a_addr = smem_u32(atile);
+  const uint32_t b_addr = smem_u32(btile);
+  constexpr uint32_t SBO = (K / 8) * 128;
+
+  double acc = (!first && valid) ? me[e] : 0.0;
+  uint32_t phase = 0;
+  bool ok = true;
+#pragma unroll 1
+  for (int ih = 0; ih < nhel && ok; ih++) {
+    const float2* row = J + (long long)ih * P::NCOL * ldj + e;
+    float mx = 0.f;
+    if (valid) {
+#pragma unroll 8
+      for (int k = 0; k < P::NCOL; k++) {
+        const float2 v = row[(long long)k * ldj];
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+      }
+    }
+    const int ex = mx > 0.f ? ((int)((__float_as_uint(mx) >> 23) & 0xff) - 127) : 0;
+    const float s = __uint_as_float((uint32_t)(127 - ex) << 23);  // 2^-ex
+#pragma unroll 1
+    for (int j = 0; j < K / 8; j++) {
+      __align__(16) __half hr[8], lr[8], hi_[8], li[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int k = 8 * j + q;
+        const float2 v = (valid && k < P::NCOL) ? row[(long long)k * ldj] : make_float2(0.f, 0.f);
+        const float xr = s * v.x, xi = s * v.y;
+        hr[q] = __float2half_rn(xr);
+        lr[q] = __float2half_rn(xr - __half2float(hr[q]));
+        hi_[q] = __float2half_rn(xi);
+        li[q] = __float2half_rn(xi - __half2float(hi_[q]));
+      }
+      const uint32_t off = tc::tile_off(tid, 8 * j, K);
+      *reinterpret_cast<uint4*>(atile + 0 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(hr);
+      *reinterpret_cast<uint4*>(atile + 1 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(lr);
+      *reinterpret_cast<uint4*>(atile + 2 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(hi_);
+      *reinterpret_cast<uint4*>(atile + 3 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(li);
+    }
+    fence_proxy_async_smem();  // generic-proxy tile writes -> visible to the tensor core
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      for (int part = 0; part < 2; part++) {  // 0: Re -> columns [0, N), 1: Im -> [N, 2N)
+        const uint32_t d = tmem + part * N;
+        for (int kk = 0; kk < K / 16; kk++) {
+          const uint64_t bd = tc::smem_desc(b_addr + kk * 2 * tc::LBO, tc::LBO, SBO);
+          const uint32_t hi_base = a_addr + (2 * part) * (uint32_t)LY::a_tile + kk * 2 * tc::LBO;
+          const uint32_t lo_base = a_addr + (2 * part + 1) * (uint32_t)LY::a_tile + kk * 2 * tc::LBO;
+          tc::mma_f16(d, tc::smem_desc(hi_base, tc::LBO, SBO), bd, idesc, kk > 0 ? 1u : 0u);
+          tc::mma_f16(d, tc::smem_desc(lo_base, tc::LBO, SBO), bd, idesc, 1u);
+        }
+      }
+      tc::mma_commit(mma_bar);
+    }
+    // bounded wait, outcome uniform across the CTA (see sigma_tc_kernel)
+    if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, WAIT_POLLS) ? 1 : 0)) {
+      if (tid == 0) atomicOr(status, ST_MMA_TIMEOUT);
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    tc::fence_after_sync();
+    float dsum = 0.f;
+#pragma unroll 1
+    for (int c = 0; c < N; c += 16) {
+      float dr[16], di[16];
+      tc::tmem_ld16(lane_base + c, dr);
+      tc::tmem_ld16(lane_base + N + c, di);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 16; q++) {
+        const int k = c + q;
+        const float2 v = (valid && k < P::NCOL) ? row[(long long)k * ldj] : make_float2(0.f, 0.f);
+        dsum = fmaf(v.x, dr[q], dsum);
+        dsum = fmaf(v.y, di[q], dsum);
+      }
+    }
+    acc += (double)(dsum / s);
+    tc::fence_before_sync();
+    __syncthreads();  // tiles and accumulators are reused by the next helicity
+  }
+  if (!ok) mbar_wait_bounded(mma_bar, phase, WAIT_POLLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, LY::tmem_cols);
+  }
+  if (ok && valid) {
+    constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+    me[e] = last ? acc * norm : acc;
+  }
+}
+
+// The two phases over slices of the good helicities, every event in each
+// launch (full grids), with a stream-ordered workspace of at most
+// ROWS_WORKSPACE bytes of flows (FP32 complex [slice][NCOL][events]).
+constexpr size_t ROWS_WORKSPACE = size_t(1) << 30;
+
+template <class P, int NT>
+int launch_sigma_rows(const LaunchArgs& a) {
+  static_assert(128 % NT == 0, "flow rows are padded to 128 events");
+  constexpr size_t smem1 = Layout<P, float, NT>::base_bytes;
+  constexpr size_t smem2 = LayoutRows<P>::base_bytes;
+  static const cudaError_t attr1 = set_smem_attr(flows_kernel<P, NT>, smem1);
+  static const cudaError_t attr2 = set_smem_attr(colour_rows_tc_kernel<P>, smem2);
+  if (attr1 != cudaSuccess || attr2 != cudaSuccess) return -4;
+  if (a.nevt <= 0 || a.nhel <= 0) return 0;
+  const long long ldj = (a.nevt + 127) / 128 * 128;
+  const size_t per_hel = (size_t)P::NCOL * (size_t)ldj * sizeof(float2);
+  long long hs = (long long)(ROWS_WORKSPACE / per_hel);
+  hs = hs < 1 ? 1 : (hs > a.nhel ? a.nhel : hs);
+  float2* J = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&J), (size_t)hs * per_hel, a.stream) != cudaSuccess) return -4;
+  for (int h0 = 0; h0 < a.nhel; h0 += (int)hs) {
+    const int nh = a.nhel - h0 < hs ? a.nhel - h0 : (int)hs;
+    flows_kernel<P, NT><<<(unsigned)((a.nevt + NT - 1) / NT), NT, smem1, a.stream>>>(
+        a.mom, a.nevt, J, ldj, a.hels + h0, nh, a.kp, a.status);
+    colour_rows_tc_kernel<P><<<(unsigned)(ldj / 128), 128, smem2, a.stream>>>(
+        J, ldj, a.nevt, a.out, nh, h0 == 0, h0 + nh == a.nhel, static_cast<const uint4*>(a.ctile), a.status);
+  }
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaFreeAsync(J, a.stream);
+  return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -4;
 }
 
 template <class P>

@@ -174,6 +174,36 @@ __global__ void __launch_bounds__(NT) sigma_kernel(const double* __restrict__ mo
   }
 }
 
+// First phase of the two-phase mixed path (processes whose colour operands do
+// not fit in shared memory next to the per-event state): the FP32 colour flows
+// of every (good helicity, event) row, written to J[(ih * NCOL + k) * ldj + e]
+// (e: event index within the launch, ldj >= the launch's events rounded up to
+// NT; consecutive events adjacent, so the stores coalesce).  The ragged tail's
+// threads repeat a valid event and write their own (padding) rows.  The
+// colour quadratic form of these rows is the second phase
+// (colour_rows_tc_kernel).
+template <class P, int NT>
+__global__ void __launch_bounds__(NT) flows_kernel(const double* __restrict__ mom, long long nevt,
+                                                   float2* __restrict__ J, long long ldj,
+                                                   const int* __restrict__ hels, int nhel, KParams kp,
+                                                   unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  using LY = Layout<P, float, NT>;
+  const int nvalid = load_and_prepare<P, float, NT>(smem, mom, nevt, kp, status);
+  if (nvalid < 0) return;
+  const float* ev = reinterpret_cast<const float*>(smem + LY::slab_off) + threadIdx.x;
+  cx<float>* jamp = reinterpret_cast<cx<float>*>(smem + LY::jamp_off) + threadIdx.x;
+  const long long e = (long long)blockIdx.x * NT + threadIdx.x;
+#pragma unroll 1
+  for (int ih = 0; ih < nhel; ih++) {
+    const int h = __ldg(hels + ih);
+    P::template amplitudes<float>(ev, NT, h, kp.v, jamp, NT);
+    float2* row = J + (long long)ih * P::NCOL * ldj + e;
+#pragma unroll 4
+    for (int k = 0; k < P::NCOL; k++) row[(long long)k * ldj] = make_float2(jamp[k * NT].re, jamp[k * NT].im);
+  }
+}
+
 // |M|^2 plus the event-by-event random choice of a helicity and a leading
 // colour flow for unweighted events (paper Sect. 5: the last ingredient needed
 // by the event files).  rnd[e] = (r_hel, r_col) in [0, 1):

@@ -27,6 +27,7 @@ from .diagrams import build_plan, count_diagrams
 
 PROCESSES = {
     "e+ e- > mu+ mu-": ("eemumu", 0),
+    "u u~ > t t~": ("uutt", 0),
     "g g > t t~": ("ggtt", 2),
     "g g > t t~ g": ("ggttg", 3),
     "g g > t t~ g g": ("ggttgg", 4),
@@ -70,6 +71,14 @@ def _colour_quadratic(K, ncol) -> list[str]:
         out.append(f"    acc = fmaf_t<R>(JAMP({i}).re, yr, acc); acc = fmaf_t<R>(JAMP({i}).im, yi, acc); }}")
     out.append("  return acc;")
     return out
+
+
+# processes whose FP32 path recomputes the external-state ingredients per
+# helicity instead of keeping them in the shared-memory slab (gg -> t t~ g g:
+# with the flows sharing the operand-tile space the CTA needs 66 KB instead of
+# 109 KB, and the freed L1 holds more of the spilled registers; measured 5 %
+# faster)
+LEAN_SLAB = set(filter(None, os.environ.get("MG_LEAN_SLAB", "ggttgg").split(",")))
 
 
 def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
@@ -130,7 +139,7 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     L.append(f"static constexpr int NSLOT_LEAN = {nslot_lean};  // slots without the external-state ingredients")
     L.append("// FP32 path: recompute the external-state ingredients per helicity instead of")
     L.append("// keeping them in shared memory (measured slower while registers bound occupancy)")
-    L.append("static constexpr bool LEAN_SLAB = false;")
+    L.append(f"static constexpr bool LEAN_SLAB = {'true' if tag in LEAN_SLAB else 'false'};")
     L.append(f"static constexpr double IDEN = {iden}.0;")
     L.append(f"static constexpr int CDEN = {cden};")
     L.append(f"static constexpr int KNUM[NCOL * NCOL] = {{{_fmt_knum(K)}}};")
@@ -148,7 +157,8 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         L.append(f"  double k{i}[4] = {{{', '.join(f'{sign}p[{4 * s + mu}]' for mu in range(4))}}};")
         for mu in range(4):
             L.append(f"  EV({sl[f'k{i}'] + mu}) = R(k{i}[{mu}]);")
-        L.append(f"  {{ double b[6]; vector_basis(p + {4 * s}, b);")
+        # the lean FP32 slab has no room for the external-state ingredients
+        L.append(f"  if constexpr (!(LEAN_SLAB && sizeof(R) == 4)) {{ double b[6]; vector_basis(p + {4 * s}, b);")
         for j in range(6):
             L.append(f"    EV({sl[f'e{i}'] + j}) = R(b[{j}]);")
         L.append("  }")
@@ -156,7 +166,7 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         fname = "ft" if name == "pt" else "ftb"
         for mu in range(4):
             L.append(f"  EV({sl[name] + mu}) = R(p[{4 * s + mu}]);")
-        L.append(f"  {{ double f[5]; fermion_ingredients(p + {4 * s}, mt, f);")
+        L.append(f"  if constexpr (!(LEAN_SLAB && sizeof(R) == 4)) {{ double f[5]; fermion_ingredients(p + {4 * s}, mt, f);")
         for j in range(5):
             L.append(f"    EV({sl[fname] + j}) = R(f[{j}]);")
         L.append("  }")
@@ -720,8 +730,6 @@ def emit_eemumu(tag: str) -> str:
     L.append("static constexpr int NDIAG = 2;")
     L.append("static constexpr int NAMP = 2;")
     L.append("static constexpr int NSLOT = 23;")
-    L.append("static constexpr int NSLOT_K = 23;")
-    L.append("static constexpr int KBASE = 0;")
     L.append("static constexpr int NSLOT_LEAN = 23;")
     L.append("static constexpr bool LEAN_SLAB = false;")
     L.append("static constexpr double IDEN = 4.0;")
@@ -776,6 +784,69 @@ def emit_eemumu(tag: str) -> str:
     return "\n".join(L) + "\n"
 
 
+def emit_uutt(tag: str) -> str:
+    """u(0) u~(1) -> t(2) t~(3): the s-channel gluon diagram.  One colour
+    structure T^a_{i_t j_tbar} T^a_{i_u j_ubar}, whose colour sum is 2 (KNUM
+    {2}, CDEN 1).  kp = {g_s, mt}; amp = (g^2 / s) (vbar gamma u).(ubar gamma v)."""
+    L = []
+    L.append("// generated by paper_2303_18244_gb300.generator for 'u u~ > t t~'")
+    L.append("#pragma once")
+    L.append('#include "mg_vertices.cuh"')
+    L.append("namespace mg {")
+    L.append(f"struct {tag} {{")
+    L.append("static constexpr int NPAR = 4;")
+    L.append("static constexpr int NHEL = 16;")
+    L.append("static constexpr int NCOL = 1;")
+    L.append("static constexpr int NDIAG = 1;")
+    L.append("static constexpr int NAMP = 1;")
+    L.append("static constexpr int NSLOT = 21;")
+    L.append("static constexpr int NSLOT_LEAN = 21;")
+    L.append("static constexpr bool LEAN_SLAB = false;")
+    L.append("static constexpr double IDEN = 36.0;")
+    L.append("static constexpr int CDEN = 1;")
+    L.append("static constexpr int KNUM[1] = {2};")
+    L.append("// per-event ingredients (FP64): spinor ingredients of the four fermions, g^2 / s")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void prepare(const double* __restrict__ p, const double* __restrict__ kp,")
+    L.append("                                        R* __restrict__ ev, const int es) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("  for (int i = 0; i < 4; i++) {")
+    L.append("    double f[5]; fermion_ingredients(p + 4 * i, i < 2 ? 0.0 : kp[1], f);")
+    L.append("    for (int j = 0; j < 5; j++) EV(5 * i + j) = R(f[j]);")
+    L.append("  }")
+    L.append("  const double P[4] = {p[0] + p[4], p[1] + p[5], p[2] + p[6], p[3] + p[7]};")
+    L.append("  const double s = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];")
+    L.append("  EV(20) = R(kp[0] * kp[0] / s);")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
+    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp,")
+    L.append("                                           const int js) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("#define ING(i) FermIngr<R>{EV(5 * (i)), EV(5 * (i) + 1), EV(5 * (i) + 2), EV(5 * (i) + 3), EV(5 * (i) + 4)}")
+    for i in range(4):
+        L.append(f"  const int l{i} = ((hel >> {3 - i}) & 1) ? 1 : -1;")
+    L.append("  const Sp<R> w0 = ext_u<R>(ING(0), l0);")
+    L.append("  const Sp<R> w1 = ext_vbar<R>(ING(1), l1);")
+    L.append("  const Sp<R> w2 = ext_ubar<R>(ING(2), l2);")
+    L.append("  const Sp<R> w3 = ext_v<R>(ING(3), l3);")
+    L.append("  const cx<R> one = {R(1), R(0)};")
+    L.append("  const V4<R> jl = ffv_vcur<R>(w1, w0, one);")
+    L.append("  const V4<R> jh = ffv_vcur<R>(w2, w3, one);")
+    L.append("  jamp[0] = EV(20) * dot(jl, jh);")
+    L.append("#undef ING")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
+    L.append("  return R(2) * (jamp[0].re * jamp[0].re + jamp[0].im * jamp[0].im);")
+    L.append("}")
+    L.append(f"}};  // struct {tag}")
+    L.append("}  // namespace mg")
+    return "\n".join(L) + "\n"
+
+
 # processes emitted as straight-line code cut into separately compiled chunk
 # functions of about CHUNK_AMPS amplitudes (one straight-line function of this
 # size does not compile in reasonable time); currents that cross a chunk
@@ -787,14 +858,17 @@ CHUNK_AMPS = int(os.environ.get("MG_CHUNK_AMPS", "40"))
 def emit(proc: str) -> tuple[str, str]:
     """(tag, header source) for a process string."""
     tag, n = PROCESSES[proc]
-    if n == 0:
+    if tag == "eemumu":
         return tag, emit_eemumu(tag)
+    if tag == "uutt":
+        return tag, emit_uutt(tag)
     return tag, emit_gg(n, tag, mode="chunked" if tag in CHUNKED else "straight")
 
 
 # threads per CTA: FP64 path / mixed path (shared-memory slab sizes differ)
 THREADS = {
     "eemumu": (128, 128),
+    "uutt": (128, 128),
     "ggtt": (128, 128),
     "ggttg": (128, 128),
     "ggttgg": (64, 128),
@@ -806,6 +880,12 @@ THREADS = {
 # operand tiles of 128 events plus FP32 colour-flow accumulators must fit in
 # shared memory next to the per-event slab)
 TENSOR_CORE_COLOUR = {"ggttg", "ggttgg"}
+# tensor-core processes whose colour flows share the operand tiles' space
+TC_ALIAS = {"ggttgg"}
+# processes whose mixed path writes the colour flows of every (helicity, event)
+# row to HBM and contracts them on the tensor cores in a second kernel
+# (120 flows: the operand tiles do not fit beside the per-event state)
+TENSOR_CORE_ROWS = set(filter(None, os.environ.get("MG_TC_ROWS", "ggttggg").split(",")))
 
 
 # processes whose vertex routines are called rather than inlined, per
@@ -825,10 +905,17 @@ def emit_tu(proc: str, prec: str) -> tuple[str, str]:
     tag, n = PROCESSES[proc]
     nt64, nt32 = THREADS[tag]
     calls = "#define MG_VERTEX __noinline__\n" if tag in VERTEX_CALLS[prec] else ""
+    if prec == "f32" and tag in TC_ALIAS:
+        calls += "#define MG_TC_ALIAS 1\n"
     head = f"// generated by paper_2303_18244_gb300.generator: {prec} kernels of '{proc}'\n{calls}"
-    tc = tag in TENSOR_CORE_COLOUR
+    tc = tag in TENSOR_CORE_COLOUR or tag in TENSOR_CORE_ROWS
     if prec == "f32":
-        mixed = f"launch_sigma_tc<{tag}>(a)" if tc else f"launch_sigma<{tag}, float, {nt32}>(a)"
+        if tag in TENSOR_CORE_ROWS:
+            mixed = f"launch_sigma_rows<{tag}, {nt32}>(a)"
+        elif tc:
+            mixed = f"launch_sigma_tc<{tag}>(a)"
+        else:
+            mixed = f"launch_sigma<{tag}, float, {nt32}>(a)"
         inc = '#include "../mg_colour_tc.cuh"\n' if tc else ""
         src = f"""{head}#include "../mg_kernels.cuh"
 {inc}#include "{tag}.cuh"

@@ -118,6 +118,40 @@ def test_ggtt_matches_analytic(mt):
     np.testing.assert_allclose(me, ggtt_analytic(p, mt, par.alpha_s), rtol=1e-12)
 
 
+def uutt_analytic(p, mt, alpha_s):
+    """q q~ -> Q Q~ at LO, averaged over initial spins and colours:
+    (4/9) g^4 [(m^2 - t)^2 + (m^2 - u)^2 + 2 m^2 s] / s^2 (textbook result)."""
+    g4 = (4 * math.pi * alpha_s) ** 2
+
+    def m2(a):
+        return a[..., 0] ** 2 - a[..., 1] ** 2 - a[..., 2] ** 2 - a[..., 3] ** 2
+
+    s = m2(p[:, 0] + p[:, 1])
+    t = m2(p[:, 0] - p[:, 2])
+    u = m2(p[:, 0] - p[:, 3])
+    m = mt * mt
+    return 4.0 / 9.0 * g4 * ((m - t) ** 2 + (m - u) ** 2 + 2 * m * s) / s ** 2
+
+
+@pytest.mark.parametrize("mt", [173.0, 0.0])
+def test_uutt_matches_analytic(mt):
+    p = process_momenta("u u~ > t t~", 1000.0, 300, 7, mt=mt)
+    par = O.Params(mt=mt)
+    me = O.me("u u~ > t t~", p, par)
+    np.testing.assert_allclose(me, uutt_analytic(p, mt, par.alpha_s), rtol=1e-12)
+
+
+def test_uutt_analytic_formula_massless_limit():
+    """Self-check of the closed form: m = 0 gives (4/9) g^4 (t^2 + u^2) / s^2."""
+    g4 = (4 * math.pi * 0.118) ** 2
+    E = 50.0
+    c = 0.3
+    p = np.array([[[E, 0, 0, E], [E, 0, 0, -E], [E, E * math.sqrt(1 - c * c), 0, E * c],
+                   [E, -E * math.sqrt(1 - c * c), 0, -E * c]]])
+    s, t, u = 4 * E * E, -2 * E * E * (1 - c), -2 * E * E * (1 + c)
+    assert abs(uutt_analytic(p, 0.0, 0.118)[0] / (4 / 9 * g4 * (t * t + u * u) / (s * s)) - 1) < 1e-14
+
+
 def test_ggtt_width_is_small_effect():
     """With Gamma_t in the t-channel propagators the result moves by O(1e-4) only."""
     p = process_momenta("g g > t t~", 1000.0, 100, 2)
