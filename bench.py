@@ -46,6 +46,7 @@ WORKLOADS = {
     "ggttgg": ("g g > t t~ g g", 1500.0, 3, 524288),
     "ggttggg": ("g g > t t~ g g g", 2000.0, 4, 65536),
     "uutt": ("u u~ > t t~", 1000.0, 7, 524288),
+    "uuttg": ("u u~ > t t~ g", 1200.0, 8, 524288),
 }
 METRIC = "gg→tt̄gg MEs/s on 1 GB300, FP64 vs mixed (≤1e-5 rel err); serve p50/p99 ms"
 L2_FLUSH_BYTES = 256 << 20

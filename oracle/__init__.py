@@ -32,6 +32,7 @@ PROCS = {
     "g g > t t~ g g": 3,
     "g g > t t~ g g g": 4,
     "u u~ > t t~": 5,
+    "u u~ > t t~ g": 6,
 }
 
 
@@ -88,6 +89,7 @@ def _declare(L):
     L.mgo_gamma.argtypes = [_D]
     L.mgo_npar.argtypes = [ctypes.c_int]
     L.mgo_flow_weights.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int64, _D]
+    L.mgo_uuttg_amps.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
     return L
 
 
@@ -245,3 +247,15 @@ def unweight(w: np.ndarray, r: np.ndarray, w_max: float) -> np.ndarray:
     r = np.asarray(r, dtype=np.float64)
     kept = [i for i in range(w.shape[0]) if r[i] * w_max < w[i]]
     return np.array(kept, dtype=np.int64)
+
+
+def uuttg_amps(mom: np.ndarray, spins, eps5, params: Params | None = None) -> np.ndarray:
+    """Colour-dressed amplitudes of u u~ -> t t~ g for one event, spins
+    (s1, s2, s3, s4) in {0, 1} and a complex gluon polarisation vector eps5[4]
+    (mgo_uuttg_amps): complex [3 (u)][3 (u~)][3 (t)][3 (t~)][8 (gluon)]."""
+    params = params or Params()
+    m = np.ascontiguousarray(mom, dtype=np.float64).reshape(20)
+    e = np.ascontiguousarray(np.asarray(eps5, dtype=np.complex128).view(np.float64))
+    out = np.empty(648 * 2, dtype=np.float64)
+    _check(lib().mgo_uuttg_amps(_p(params.array()), _p(m), *[int(x) for x in spins], _p(e), _p(out)))
+    return out.view(np.complex128).reshape(3, 3, 3, 3, 8)

@@ -69,7 +69,7 @@ static const real PI_R = 3.14159265358979323846264338327950288L;
 #define MGO_ERR_ARG (-1)
 #define MGO_ERR_NOMEM (-2)
 
-enum { MGO_EEMUMU = 0, MGO_GGTT = 1, MGO_GGTTG = 2, MGO_GGTTGG = 3, MGO_GGTTGGG = 4, MGO_UUTT = 5 };
+enum { MGO_EEMUMU = 0, MGO_GGTT = 1, MGO_GGTTG = 2, MGO_GGTTGG = 3, MGO_GGTTGGG = 4, MGO_UUTT = 5, MGO_UUTTG = 6 };
 
 #define MAXG 5     /* at most 5 gluons */
 #define MAXPERM 120
@@ -894,6 +894,198 @@ static real me_uutt(const oparams* o, const real* mom) {
   return sum * colour / 36.0;
 }
 
+/* u(p1) u~(p2) -> t(p3) t~(p4) g(p5): the five diagrams written out with
+ * explicit Dirac matrices (Feynman rules above; light quark massless):
+ *   D1 gluon off the u line at the u end,  D2 at the u~ end,
+ *   D3 off the top line at the t end,       D4 at the t~ end,
+ *   D5 three-gluon vertex on the s-channel gluon.
+ * Colour: each diagram's colour factor for every assignment (u i, u~ j, t k,
+ * t~ l, gluon a) is an explicit sum over Gell-Mann generators and f^{abc}:
+ *   D1 sum_b (T^b T^a)_{ji} T^b_{kl},  D2 sum_b (T^a T^b)_{ji} T^b_{kl},
+ *   D3 sum_b T^b_{ji} (T^a T^b)_{kl},  D4 sum_b T^b_{ji} (T^b T^a)_{kl},
+ *   D5 sum_{bc} f^{bca} T^b_{ji} T^c_{kl}.
+ * IDEN = 4 spins x 9 colours. */
+static cplx UUTTG_COL[5][3][3][3][3][8]; /* [diagram][i][j][k][l][a] */
+static int uuttg_col_ready = 0;
+static pthread_mutex_t uuttg_lock = PTHREAD_MUTEX_INITIALIZER;
+
+static void init_uuttg_colour(void) {
+  init_fabc();
+  pthread_mutex_lock(&uuttg_lock);
+  if (!uuttg_col_ready) {
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++)
+        for (int k = 0; k < 3; k++)
+          for (int l = 0; l < 3; l++)
+            for (int a = 0; a < 8; a++) {
+              cplx c[5] = {0, 0, 0, 0, 0};
+              for (int b = 0; b < 8; b++) {
+                cplx ba_ji = 0, ab_ji = 0, ab_kl = 0, ba_kl = 0;
+                for (int m = 0; m < 3; m++) {
+                  ba_ji += TGEN[b][j][m] * TGEN[a][m][i];
+                  ab_ji += TGEN[a][j][m] * TGEN[b][m][i];
+                  ab_kl += TGEN[a][k][m] * TGEN[b][m][l];
+                  ba_kl += TGEN[b][k][m] * TGEN[a][m][l];
+                }
+                c[0] += ba_ji * TGEN[b][k][l];
+                c[1] += ab_ji * TGEN[b][k][l];
+                c[2] += TGEN[b][j][i] * ab_kl;
+                c[3] += TGEN[b][j][i] * ba_kl;
+                for (int cc = 0; cc < 8; cc++) c[4] += FABC[b][cc][a] * TGEN[b][j][i] * TGEN[cc][k][l];
+              }
+              for (int d = 0; d < 5; d++) UUTTG_COL[d][i][j][k][l][a] = c[d];
+            }
+    uuttg_col_ready = 1;
+  }
+  pthread_mutex_unlock(&uuttg_lock);
+}
+
+/* The five colour-stripped diagram values for fixed spins and a given
+ * (complex) polarisation vector eps5 of the outgoing gluon (eps5 = k5 gives
+ * the Ward identity). */
+static void uuttg_diagrams(const oparams* o, const real* mom, int s1, int s2, int s3, int s4, const cplx eps5[4],
+                           cplx A[5]) {
+  const real* p1 = mom;
+  const real* p2 = mom + 4;
+  const real* p3 = mom + 8;
+  const real* p4 = mom + 12;
+  const real* p5 = mom + 16;
+  const real g = sqrt(4.0 * PI_R * o->alpha_s);
+  const real mt = o->mt;
+  cplx u1[4], v2[4], vb2[4], u3[4], ub3[4], v4[4];
+  spinor_u(p1, 0.0, s1, u1);
+  spinor_v(p2, 0.0, s2, v2);
+  dirac_bar(v2, vb2);
+  spinor_u(p3, mt, s3, u3);
+  dirac_bar(u3, ub3);
+  spinor_v(p4, mt, s4, v4);
+  cplx E[4][4];
+  slash_c(eps5, E);
+  real q34[4], s12[4], a[4], b[4], c[4], d[4];
+  for (int mu = 0; mu < 4; mu++) {
+    q34[mu] = p3[mu] + p4[mu];
+    s12[mu] = p1[mu] + p2[mu];
+    a[mu] = p1[mu] - p5[mu];   /* D1 light propagator */
+    b[mu] = p5[mu] - p2[mu];   /* D2 light propagator (along the fermion flow) */
+    c[mu] = p3[mu] + p5[mu];   /* D3 top propagator */
+    d[mu] = -p4[mu] - p5[mu];  /* D4 top propagator (along the fermion flow) */
+  }
+  const real q2 = dot_rr(q34, q34), s = dot_rr(s12, s12);
+  const cplx iw = I * mt * o->wt;
+  /* propagator matrices: massless i qslash / q^2, top i (qslash + m) / (q^2 - m^2 + i m w) */
+  cplx SA[4][4], SB[4][4], SC[4][4], SD[4][4];
+  slash_r(a, SA);
+  slash_r(b, SB);
+  slash_r(c, SC);
+  slash_r(d, SD);
+  const cplx fa = I / dot_rr(a, a), fb = I / dot_rr(b, b);
+  const cplx fc = I / (dot_rr(c, c) - mt * mt + iw), fd = I / (dot_rr(d, d) - mt * mt + iw);
+  for (int r = 0; r < 4; r++)
+    for (int cc = 0; cc < 4; cc++) {
+      SA[r][cc] *= fa;
+      SB[r][cc] *= fb;
+      SC[r][cc] = (SC[r][cc] + (r == cc ? mt : 0.0)) * fc;
+      SD[r][cc] = (SD[r][cc] + (r == cc ? mt : 0.0)) * fd;
+    }
+  const cplx ig = I * g;
+  /* vertex-dressed spinors */
+  cplx Eu1[4], SAEu1[4], vb2E[4], vb2ESB[4], ub3E[4], ub3ESC[4], Ev4[4], SDEv4[4];
+  matcol((const cplx(*)[4])E, u1, Eu1);
+  matcol((const cplx(*)[4])SA, Eu1, SAEu1);
+  rowmat(vb2, (const cplx(*)[4])E, vb2E);
+  rowmat(vb2E, (const cplx(*)[4])SB, vb2ESB);
+  rowmat(ub3, (const cplx(*)[4])E, ub3E);
+  rowmat(ub3E, (const cplx(*)[4])SC, ub3ESC);
+  matcol((const cplx(*)[4])E, v4, Ev4);
+  matcol((const cplx(*)[4])SD, Ev4, SDEv4);
+  cplx L[4], H[4], L1[4], L2[4], H3[4], H4[4];
+  for (int mu = 0; mu < 4; mu++) {
+    cplx t[4];
+    matcol((const cplx(*)[4])GAM[mu], u1, t);
+    L[mu] = ig * rowcol(vb2, t);                  /* vbar2 (i g gamma^mu) u1 */
+    L2[mu] = ig * ig * rowcol(vb2ESB, t);         /* vbar2 (ig eps) S_B (ig gamma^mu) u1 */
+    matcol((const cplx(*)[4])GAM[mu], SAEu1, t);
+    L1[mu] = ig * ig * rowcol(vb2, t);            /* vbar2 (ig gamma^mu) S_A (ig eps) u1 */
+    matcol((const cplx(*)[4])GAM[mu], v4, t);
+    H[mu] = ig * rowcol(ub3, t);                  /* ubar3 (i g gamma^mu) v4 */
+    H3[mu] = ig * ig * rowcol(ub3ESC, t);         /* ubar3 (ig eps) S_C (ig gamma^mu) v4 */
+    matcol((const cplx(*)[4])GAM[mu], SDEv4, t);
+    H4[mu] = ig * ig * rowcol(ub3, t);            /* ubar3 (ig gamma^mu) S_D (ig eps) v4 */
+  }
+  /* gluon propagators -i g_{mu nu} / k^2 */
+  A[0] = dot_cc(L1, H) * (-I / q2);
+  A[1] = dot_cc(L2, H) * (-I / q2);
+  A[2] = dot_cc(L, H3) * (-I / s);
+  A[3] = dot_cc(L, H4) * (-I / s);
+  /* three-gluon vertex with incoming (b, mu, P = p1 + p2), (c, nu, -q34),
+   * (a, rho, -p5): g [g^{mu nu}(P + q34)^rho + g^{nu rho}(p5 - q34)^mu
+   * + g^{rho mu}(-p5 - P)^nu], times f^{bca} (in the colour factor) */
+  const cplx GL[4] = {L[0] * (-I / s), L[1] * (-I / s), L[2] * (-I / s), L[3] * (-I / s)};
+  const cplx GH[4] = {H[0] * (-I / q2), H[1] * (-I / q2), H[2] * (-I / q2), H[3] * (-I / q2)};
+  real x[4], y[4], z[4];
+  for (int mu = 0; mu < 4; mu++) {
+    x[mu] = s12[mu] + q34[mu];
+    y[mu] = p5[mu] - q34[mu];
+    z[mu] = -p5[mu] - s12[mu];
+  }
+  A[4] = g * (dot_cc(GL, GH) * dot_rc(x, eps5) + dot_cc(GH, eps5) * dot_rc(y, GL) + dot_cc(eps5, GL) * dot_rc(z, GH));
+}
+
+static real me_uuttg(const oparams* o, const real* mom) {
+  init_uuttg_colour();
+  real sum = 0.0;
+  for (int s1 = 0; s1 < 2; s1++)
+    for (int s2 = 0; s2 < 2; s2++)
+      for (int s3 = 0; s3 < 2; s3++)
+        for (int s4 = 0; s4 < 2; s4++)
+          for (int pol = 0; pol < 2; pol++) {
+            real e[4];
+            polarisation(mom + 16, pol, e);
+            const cplx eps[4] = {e[0], e[1], e[2], e[3]};
+            cplx A[5];
+            uuttg_diagrams(o, mom, s1, s2, s3, s4, eps, A);
+            for (int i = 0; i < 3; i++)
+              for (int j = 0; j < 3; j++)
+                for (int k = 0; k < 3; k++)
+                  for (int l = 0; l < 3; l++)
+                    for (int a = 0; a < 8; a++) {
+                      cplx m = 0;
+                      for (int dg = 0; dg < 5; dg++) m += UUTTG_COL[dg][i][j][k][l][a] * A[dg];
+                      sum += creal(m * conj(m));
+                    }
+          }
+  return sum / 36.0;
+}
+
+/* Colour-dressed amplitudes of u u~ -> t t~ g for given spins and a complex
+ * gluon polarisation vector: out[(((i*3+j)*3+k)*3+l)*8+a] (complex
+ * interleaved, 648 entries).  Test hook (Ward identity: eps5 = k5). */
+int mgo_uuttg_amps(const double* params, const double* mom, int s1, int s2, int s3, int s4,
+                   const double* eps5 /* complex [4] */, double* out) {
+  oparams o;
+  unpack_params(params, &o);
+  init_uuttg_colour();
+  real p[20];
+  for (int i = 0; i < 20; i++) p[i] = mom[i];
+  cplx e[4];
+  for (int mu = 0; mu < 4; mu++) e[mu] = eps5[2 * mu] + I * eps5[2 * mu + 1];
+  cplx A[5];
+  uuttg_diagrams(&o, p, s1, s2, s3, s4, e, A);
+  int n = 0;
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++)
+      for (int k = 0; k < 3; k++)
+        for (int l = 0; l < 3; l++)
+          for (int a = 0; a < 8; a++) {
+            cplx m = 0;
+            for (int dg = 0; dg < 5; dg++) m += UUTTG_COL[dg][i][j][k][l][a] * A[dg];
+            out[2 * n] = (double)creal(m);
+            out[2 * n + 1] = (double)cimag(m);
+            n++;
+          }
+  return MGO_OK;
+}
+
 /* g(p1) g(p2) -> t(p3) t~(p4) g(p5) ... : n gluons in total.
  * flow_w (may be NULL): sum over spin states of |A(sigma)|^2 per ordering. */
 static real me_ggtt_ng_w(const oparams* o, int n, const real* mom, real* flow_w);
@@ -969,6 +1161,7 @@ static int proc_gluons(int proc) {
 
 int mgo_npar(int proc) {
   if (proc == MGO_EEMUMU || proc == MGO_UUTT) return 4;
+  if (proc == MGO_UUTTG) return 5;
   const int n = proc_gluons(proc);
   return n ? n + 2 : MGO_ERR_ARG;
 }
@@ -1004,6 +1197,7 @@ int mgo_me(int proc, const double* params, const double* mom, int64_t nevt, doub
     for (int i = 0; i < npar * 4; i++) p[i] = mom[(size_t)e * npar * 4 + i];
     me[e] = (double)((proc == MGO_EEMUMU) ? me_eemumu(&o, p)
                      : (proc == MGO_UUTT) ? me_uutt(&o, p)
+                     : (proc == MGO_UUTTG) ? me_uuttg(&o, p)
                                           : me_ggtt_ng(&o, proc_gluons(proc), p));
   }
   return MGO_OK;

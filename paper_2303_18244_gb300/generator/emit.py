@@ -28,6 +28,7 @@ from .diagrams import build_plan, count_diagrams
 PROCESSES = {
     "e+ e- > mu+ mu-": ("eemumu", 0),
     "u u~ > t t~": ("uutt", 0),
+    "u u~ > t t~ g": ("uuttg", 0),
     "g g > t t~": ("ggtt", 2),
     "g g > t t~ g": ("ggttg", 3),
     "g g > t t~ g g": ("ggttgg", 4),
@@ -847,6 +848,133 @@ def emit_uutt(tag: str) -> str:
     return "\n".join(L) + "\n"
 
 
+def emit_uuttg(tag: str) -> str:
+    """u(0) u~(1) -> t(2) t~(3) g(4): five diagrams (gluon off the u end, the
+    u~ end, the t end, the t~ end, three-gluon vertex on the s-channel gluon),
+    Feynman rules with vertices i g gamma^mu T^a and g f^{abc} V3, gluon
+    propagator -i g_{mu nu}/k^2, quark propagator i (qslash + m)/(q^2 - m^2
+    + i m Gamma).  Colour: four flows (generator.colour_two_lines) with the
+    decomposition and colour matrix computed there.  kp = {g_s, mt, Gamma_t}.
+    Slab (per event, FP64 set-up): spinor ingredients of the four fermions,
+    the gluon's transverse basis, the propagator momenta and coefficients."""
+    from .colour_two_lines import colour_matrix, decomposition
+    dec = decomposition()
+    C = colour_matrix()
+    cden, K = common_denominator(C)
+    L = []
+    L.append("// generated by paper_2303_18244_gb300.generator for 'u u~ > t t~ g'")
+    L.append("#pragma once")
+    L.append('#include "mg_vertices.cuh"')
+    L.append("namespace mg {")
+    L.append(f"struct {tag} {{")
+    L.append("static constexpr int NPAR = 5;")
+    L.append("static constexpr int NHEL = 32;")
+    L.append("static constexpr int NCOL = 4;")
+    L.append("static constexpr int NDIAG = 5;")
+    L.append("static constexpr int NAMP = 5;")
+    L.append("static constexpr int NSLOT = 60;")
+    L.append("static constexpr int NSLOT_LEAN = 60;")
+    L.append("static constexpr bool LEAN_SLAB = false;")
+    L.append("static constexpr double IDEN = 36.0;")
+    L.append(f"static constexpr int CDEN = {cden};")
+    L.append(f"static constexpr int KNUM[NCOL * NCOL] = {{{_fmt_knum(K)}}};")
+    # slab: 0-19 fermion ingredients, 20-25 gluon basis, 26-29 qA = p1 - p5,
+    # 30-33 qB = p5 - p2, 34-37 qC = p3 + p5, 38-41 qD = -p4 - p5, 42-45 P = p1 + p2,
+    # 46-49 -q34, 50 cA, 51 cB, 52-53 cC, 54-55 cD, 56 1/q34^2, 57 1/s
+    L.append("// per-event set-up (FP64): spinor ingredients, gluon basis, propagator momenta")
+    L.append("// and coefficients (i g)(i / denominator)")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void prepare(const double* __restrict__ p, const double* __restrict__ kp,")
+    L.append("                                        R* __restrict__ ev, const int es) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("  const double g = kp[0], mt = kp[1], wt = kp[2];")
+    L.append("  for (int i = 0; i < 4; i++) {")
+    L.append("    double f[5]; fermion_ingredients(p + 4 * i, i < 2 ? 0.0 : mt, f);")
+    L.append("    for (int j = 0; j < 5; j++) EV(5 * i + j) = R(f[j]);")
+    L.append("  }")
+    L.append("  { double b[6]; vector_basis(p + 16, b); for (int j = 0; j < 6; j++) EV(20 + j) = R(b[j]); }")
+    L.append("  double q[6][4];")
+    L.append("  for (int mu = 0; mu < 4; mu++) {")
+    L.append("    q[0][mu] = p[mu] - p[16 + mu];")
+    L.append("    q[1][mu] = p[16 + mu] - p[4 + mu];")
+    L.append("    q[2][mu] = p[8 + mu] + p[16 + mu];")
+    L.append("    q[3][mu] = -p[12 + mu] - p[16 + mu];")
+    L.append("    q[4][mu] = p[mu] + p[4 + mu];")
+    L.append("    q[5][mu] = -p[8 + mu] - p[12 + mu];")
+    L.append("  }")
+    L.append("  for (int k = 0; k < 6; k++)")
+    L.append("    for (int mu = 0; mu < 4; mu++) EV(26 + 4 * k + mu) = R(q[k][mu]);")
+    L.append("  double m2[6];")
+    L.append("  for (int k = 0; k < 6; k++) m2[k] = q[k][0] * q[k][0] - q[k][1] * q[k][1] - q[k][2] * q[k][2] - q[k][3] * q[k][3];")
+    L.append("  EV(50) = R(-g / m2[0]);")
+    L.append("  EV(51) = R(-g / m2[1]);")
+    L.append("  for (int k = 2; k < 4; k++) {")
+    L.append("    const double dre = m2[k] - mt * mt, dim = mt * wt, r = -g / (dre * dre + dim * dim);")
+    L.append("    EV(52 + 2 * (k - 2)) = R(r * dre); EV(53 + 2 * (k - 2)) = R(-r * dim);")
+    L.append("  }")
+    L.append("  EV(56) = R(1.0 / m2[5]);")
+    L.append("  EV(57) = R(1.0 / m2[4]);")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
+    L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp,")
+    L.append("                                           const int js) {")
+    L.append("#define EV(k) ev[(k) * es]")
+    L.append("#define ING(i) FermIngr<R>{EV(5 * (i)), EV(5 * (i) + 1), EV(5 * (i) + 2), EV(5 * (i) + 3), EV(5 * (i) + 4)}")
+    L.append("#define MOM(k) M4<R>{{EV(k), EV((k) + 1), EV((k) + 2), EV((k) + 3)}}")
+    L.append("  const R g = R(kp[0]), mt = R(kp[1]);")
+    for i in range(5):
+        L.append(f"  const int l{i} = ((hel >> {4 - i}) & 1) ? 1 : -1;")
+    L.append("  const Sp<R> w0 = ext_u<R>(ING(0), l0);")
+    L.append("  const Sp<R> w1 = ext_vbar<R>(ING(1), l1);")
+    L.append("  const Sp<R> w2 = ext_ubar<R>(ING(2), l2);")
+    L.append("  const Sp<R> w3 = ext_v<R>(ING(3), l3);")
+    L.append("  const R e1[3] = {EV(20), EV(21), EV(22)}, e2[3] = {EV(23), EV(24), EV(25)};")
+    L.append("  const V4<R> eps = ext_vector<R>(e1, e2, R(l4), true);")
+    L.append("  const cx<R> ig = {R(0), g};")
+    L.append("  const cx<R> mi_q2 = {R(0), -EV(56)}, mi_s = {R(0), -EV(57)};  // -i/q34^2, -i/s")
+    L.append("  const V4<R> Lc = ffv_vcur<R>(w1, w0, ig);  // vbar2 (i g gamma) u1")
+    L.append("  const V4<R> Hc = ffv_vcur<R>(w2, w3, ig);  // ubar3 (i g gamma) v4")
+    L.append("  const Sp<R> sA = ffv_col<R>(eps, w0, MOM(26), R(0), cx<R>{EV(50), R(0)});")
+    L.append("  const Sp<R> sB = ffv_row<R>(w1, eps, MOM(30), R(0), cx<R>{EV(51), R(0)});")
+    L.append("  const Sp<R> sC = ffv_row<R>(w2, eps, MOM(34), mt, cx<R>{EV(52), EV(53)});")
+    L.append("  const Sp<R> sD = ffv_col<R>(eps, w3, MOM(38), mt, cx<R>{EV(54), EV(55)});")
+    L.append("  cx<R> A[5];")
+    L.append("  A[0] = mi_q2 * dot(ffv_vcur<R>(w1, sA, ig), Hc);")
+    L.append("  A[1] = mi_q2 * dot(ffv_vcur<R>(sB, w0, ig), Hc);")
+    L.append("  A[2] = mi_s * dot(Lc, ffv_vcur<R>(sC, w3, ig));")
+    L.append("  A[3] = mi_s * dot(Lc, ffv_vcur<R>(w2, sD, ig));")
+    L.append("  V4<R> GL, GH;")
+    L.append("  for (int mu = 0; mu < 4; mu++) {")
+    L.append("    GL.c[mu] = mi_s * Lc.c[mu];")
+    L.append("    GH.c[mu] = mi_q2 * Hc.c[mu];")
+    L.append("  }")
+    L.append("  A[4] = vvv_amp<R>(MOM(42), GL, MOM(46), GH, eps, g);")
+    for m in range(4):
+        terms = []
+        for d in range(5):
+            re, im = dec[d][m]
+            if re == 0 and im == 0:
+                continue
+            terms.append(f"cx<R>{{R({float(re)!r}), R({float(im)!r})}} * A[{d}]")
+        L.append(f"  jamp[{m} * js] = " + " + ".join(terms) + ";")
+    L.append("#undef MOM")
+    L.append("#undef ING")
+    L.append("#undef EV")
+    L.append("}")
+    L.append("// sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j); |M|^2 colour sum = result / CDEN")
+    L.append("template <typename R>")
+    L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
+    L.append("#define JAMP(k) jamp[(k) * js]")
+    L.extend(_colour_quadratic(K, 4))
+    L.append("#undef JAMP")
+    L.append("}")
+    L.append(f"}};  // struct {tag}")
+    L.append("}  // namespace mg")
+    return "\n".join(L) + "\n"
+
+
 # processes emitted as straight-line code cut into separately compiled chunk
 # functions of about CHUNK_AMPS amplitudes (one straight-line function of this
 # size does not compile in reasonable time); currents that cross a chunk
@@ -862,6 +990,8 @@ def emit(proc: str) -> tuple[str, str]:
         return tag, emit_eemumu(tag)
     if tag == "uutt":
         return tag, emit_uutt(tag)
+    if tag == "uuttg":
+        return tag, emit_uuttg(tag)
     return tag, emit_gg(n, tag, mode="chunked" if tag in CHUNKED else "straight")
 
 
@@ -869,6 +999,7 @@ def emit(proc: str) -> tuple[str, str]:
 THREADS = {
     "eemumu": (128, 128),
     "uutt": (128, 128),
+    "uuttg": (128, 128),
     "ggtt": (128, 128),
     "ggttg": (128, 128),
     "ggttgg": (64, 128),
@@ -895,6 +1026,10 @@ TENSOR_CORE_ROWS = set(filter(None, os.environ.get("MG_TC_ROWS", "ggttggg").spli
 # streams from L2 on every helicity; the FP64 path of gg -> t t~ g g (bound by
 # the FP64 pipe) and the smaller processes keep the inlined code
 VERTEX_CALLS = {"f32": {"ggttgg", "ggttggg"}, "f64": {"ggttggg"}}
+
+
+# colour-flow counts of the processes written by hand (gg processes: n!)
+FIXED_NCOL = {"eemumu": 1, "uutt": 1, "uuttg": 4}
 
 
 def emit_tu(proc: str, prec: str) -> tuple[str, str]:
@@ -926,7 +1061,7 @@ int select_{tag}_mixed(const LaunchArgs& a) {{ return launch_select<{tag}, float
 }}  // namespace mg
 """
         return tag, src
-    ncol = 1 if n == 0 else math.factorial(n)
+    ncol = FIXED_NCOL.get(tag) or math.factorial(n)
     tck = ((ncol + 15) // 16) * 16 if tc else 0
     src = f"""{head}#include "../mg_kernels.cuh"
 #include "{tag}.cuh"

@@ -24,10 +24,12 @@ WORKLOADS = {
     "g g > t t~ g g": (1500.0, 3, 300, 524288),
     "g g > t t~ g g g": (2000.0, 4, 130, 65536),
     "u u~ > t t~": (1000.0, 7, 1000, 524288),
+    "u u~ > t t~ g": (1200.0, 8, 500, 524288),
 }
 PROCS = list(WORKLOADS)
 TAGS = {"e+ e- > mu+ mu-": "eemumu", "g g > t t~": "ggtt", "g g > t t~ g": "ggttg",
-        "g g > t t~ g g": "ggttgg", "g g > t t~ g g g": "ggttggg", "u u~ > t t~": "uutt"}
+        "g g > t t~ g g": "ggttgg", "g g > t t~ g g g": "ggttggg", "u u~ > t t~": "uutt",
+        "u u~ > t t~ g": "uuttg"}
 
 
 def _ids(p):
@@ -176,6 +178,20 @@ def test_good_helicities_eemumu():
         if l[0] == -l[1] and l[2] == -l[3]:
             want.add(i)
     assert good == want
+
+
+@pytest.mark.parametrize("proc", ["u u~ > t t~", "u u~ > t t~ g"], ids=["uutt", "uuttg"])
+def test_good_helicities_light_quark_chirality(proc):
+    """The massless u u~ pair couples through a vector current: exactly the
+    helicity states with opposite u and u~ helicities survive (every top and
+    gluon helicity does)."""
+    rs, seed, _, _ = WORKLOADS[proc]
+    h = mg.Process(proc)
+    npar = h.info.npar
+    n, mask = mg.good_helicities(h, _dev(process_momenta(proc, rs, 1024, seed + 1000)))
+    good = {i for i in range(1 << npar) if mask[i]}
+    want = {i for i in range(1 << npar) if ((i >> (npar - 1)) & 1) != ((i >> (npar - 2)) & 1)}
+    assert good == want and n == len(want)
 
 
 @pytest.mark.parametrize("proc", PROCS, ids=_ids)

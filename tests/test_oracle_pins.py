@@ -345,3 +345,52 @@ def test_eemumu_lorentz_invariance_with_z_width():
     me = O.me("e+ e- > mu+ mu-", p)
     q = _boost_rotate(p, [0.1, 0.4, -0.3], [0, 1, 1], 1.1)
     np.testing.assert_allclose(O.me("e+ e- > mu+ mu-", q), me, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# u u~ -> t t~ g: five diagrams with explicit colour factors
+# --------------------------------------------------------------------------
+
+def test_uuttg_ward_identity():
+    """eps(gluon) -> k(gluon) annihilates the colour-dressed amplitude of every
+    colour assignment and spin state (Gamma_t = 0): fixes the relative signs
+    and phases of the quark-line emissions and the three-gluon diagram."""
+    par = O.Params(wt=0.0)
+    p = process_momenta("u u~ > t t~ g", 1200.0, 3, 41)
+    e = np.array([0.0, 0.6, 0.8, 0.0], dtype=complex)
+    for ev in range(p.shape[0]):
+        all_spins = [tuple((s >> (3 - i)) & 1 for i in range(4)) for s in range(16)]
+        ref = max(np.abs(O.uuttg_amps(p[ev], sp, e, par)).max() for sp in all_spins)
+        assert ref > 0
+        for spins in all_spins:
+            ward = np.abs(O.uuttg_amps(p[ev], spins, p[ev, 4].astype(complex), par)).max()
+            assert ward <= 1e-12 * ref * p[ev, 4, 0]
+
+
+def test_uuttg_width_breaks_ward_identity_only_slightly():
+    p = process_momenta("u u~ > t t~ g", 1200.0, 1, 41)
+    e = np.array([0.0, 0.6, 0.8, 0.0], dtype=complex)
+    ref = np.abs(O.uuttg_amps(p[0], (0, 1, 0, 1), e)).max()
+    ward = np.abs(O.uuttg_amps(p[0], (0, 1, 0, 1), p[0, 4].astype(complex))).max()
+    assert 1e-9 * ref * p[0, 4, 0] < ward < 1e-1 * ref * p[0, 4, 0]
+
+
+def test_uuttg_me_is_the_sum_of_the_dressed_amplitudes():
+    p = process_momenta("u u~ > t t~ g", 1200.0, 2, 42)
+    me = O.me("u u~ > t t~ g", p)
+    for ev in range(2):
+        tot = 0.0
+        for s in range(16):
+            spins = tuple((s >> (3 - i)) & 1 for i in range(4))
+            for w in range(2):
+                eps = O.polarisation(p[ev, 4], w).astype(complex)
+                tot += np.sum(np.abs(O.uuttg_amps(p[ev], spins, eps)) ** 2)
+        assert abs(tot / 36.0 / me[ev] - 1) < 1e-12
+
+
+def test_uuttg_lorentz_invariance():
+    par = O.Params(wt=0.0)
+    p = process_momenta("u u~ > t t~ g", 1200.0, 20, 43)
+    me = O.me("u u~ > t t~ g", p, par)
+    q = _boost_rotate(p, [0.3, -0.2, 0.5], [1, 2, 3], 0.7)
+    np.testing.assert_allclose(O.me("u u~ > t t~ g", q, par), me, rtol=1e-11)
