@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # kernel from one ncu capture of the current kernel on a small case: workload
 # -> (events captured, bytes); scaled to a launch by its events (the traffic
 # is per event: momenta in, |M|^2 out).  Set to None when the kernel changes.
-NCU_TRAFFIC = {"ggttgg": None}
+NCU_TRAFFIC = {"ggttgg": (65536, 12.798720e6 + 9.216e3)}  # sigma_tc_kernel_ggttgg_mixed_65536ev.md (D)
 
 SERVE_PROCS = {  # process -> sqrt(s)
     "e+ e- > mu+ mu-": 500.0,
@@ -257,8 +257,15 @@ def main():
     outp = torch.empty(nevt, dtype=torch.float64, device="cuda")
     ms_pap = timed(hpap, outp, 1, 1)
     assert mg.process_status(hpap) == 0
+    # the paper's float mode (every step in FP32)
+    hflt = mg.Process(PROC, precision=mg.MG_FLOAT)
+    mg.good_helicities(hflt, torch.from_numpy(calib).cuda())
+    outf = torch.empty(nevt, dtype=torch.float64, device="cuda")
+    ms_flt = timed(hflt, outf, 1, 1)
+    assert mg.process_status(hflt) == 0
 
-    t_mix, t_64, t_pap = max_over_ranks([sum(ms_mix), sum(ms_64) / len(ms_64), sum(ms_pap)], device="cuda")
+    t_mix, t_64, t_pap, t_flt = max_over_ranks([sum(ms_mix), sum(ms_64) / len(ms_64), sum(ms_pap), sum(ms_flt)],
+                                               device="cuda")
     value = world * nevt * args.steps / (t_mix * 1e-3)
     value64 = world * nevt / (t_64 * 1e-3)
 
@@ -267,6 +274,7 @@ def main():
     a = out.cpu().numpy()
     b = out64.cpu().numpy()
     rel = np.abs(a - b) / np.abs(b)
+    rel_f = np.abs(outf.cpu().numpy() - b) / np.abs(b)
 
     # end to end through the C ABI from pinned host buffers
     hp = torch.from_numpy(p).pin_memory()
@@ -306,6 +314,10 @@ def main():
                               "frac": achieved64 / peak64, "peak_source": "measured FP64 FMA loop (mg_diag)"}},
         "paper_mixed": {"value": world * nevt / (t_pap * 1e-3), "unit": "MEs/s",
                         "what": "FP64 diagrams + FP32 colour algebra (the paper's mixed mode)"},
+        "float": {"value": world * nevt / (t_flt * 1e-3), "unit": "MEs/s",
+                  "what": "every step in FP32 (the paper's float mode)",
+                  "accuracy_vs_fp64": {"median": float(np.median(rel_f)), "p99": float(np.quantile(rel_f, 0.99)),
+                                       "max": float(rel_f.max())}},
         "accuracy_mixed_vs_fp64": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
                                    "max": float(rel.max()), "events": nevt},
         "e2e": {"value": world * nevt / (e2e_t * 1e-3), "unit": "MEs/s",

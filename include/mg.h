@@ -60,6 +60,10 @@ extern "C" {
                        accumulation, FP64 helicity sum                            */
 #define MG_MIXED_PAPER 2 /* the paper's "mixed" (Sect. 3): Feynman diagrams in FP64,
                        colour algebra in FP32 on CUDA cores, FP64 helicity sum    */
+#define MG_FLOAT 3  /* the paper's "float" (Sect. 3): every step in FP32, the
+                       per-event set-up and propagator denominators included;
+                       colour sum on CUDA cores.  mg_sigma_select in this mode
+                       runs as in MG_MIXED                                        */
 
 /* flags */
 #define MG_NO_TOP_WIDTH 1   /* Gamma_t = 0 in every top propagator                 */
@@ -73,7 +77,7 @@ typedef struct {
   double wz;           /* Z width [GeV]                        default 2.441404  */
   double alpha_em_inv; /* 1/alpha_em                           default 132.507   */
   double gf;           /* Fermi constant [GeV^-2]              default 1.16639e-5 */
-  int precision;       /* MG_FP64, MG_MIXED or MG_MIXED_PAPER                   */
+  int precision;       /* MG_FP64, MG_MIXED, MG_MIXED_PAPER or MG_FLOAT         */
   int flags;           /* MG_NO_TOP_WIDTH | MG_PHOTON_ONLY                      */
 } mg_params;
 

@@ -105,10 +105,11 @@ struct Layout {
   static constexpr size_t base_bytes = jamp_off + ((union_bytes + 127) / 128) * 128;
 };
 
-// A1 + A2: stage the tile, run the per-event FP64 set-up into the slab.
-// Returns the number of valid events in the tile, or -1 after a timed-out copy
-// (uniformly for the whole CTA).
-template <class P, typename R, int NT>
+// A1 + A2: stage the tile, run the per-event set-up (arithmetic type D: FP64,
+// or FP32 in the all-float mode) into the slab.  Returns the number of valid
+// events in the tile, or -1 after a timed-out copy (uniformly for the whole
+// CTA).
+template <class P, typename R, int NT, typename D = double>
 __device__ __forceinline__ int load_and_prepare_at(uint64_t* bar, double* stage, R* slab,
                                                    const double* __restrict__ mom, long long nevt,
                                                    const KParams& kp, unsigned* status) {
@@ -134,43 +135,44 @@ __device__ __forceinline__ int load_and_prepare_at(uint64_t* bar, double* stage,
     return -1;
   }
   const int le = tid < nvalid ? tid : nvalid - 1;  // ragged tail: repeat a valid event
-  P::template prepare<R>(stage + le * P::NPAR * 4, kp.v, slab + tid, NT);
+  P::template prepare<R, D>(stage + le * P::NPAR * 4, kp.v, slab + tid, NT);
   __syncthreads();  // every thread is done with the momenta tile (its space is reused)
   return nvalid;
 }
 
-template <class P, typename R, int NT>
+template <class P, typename R, int NT, typename D = double>
 __device__ __forceinline__ int load_and_prepare(unsigned char* smem, const double* __restrict__ mom, long long nevt,
                                                 const KParams& kp, unsigned* status) {
   using LY = Layout<P, R, NT>;
-  return load_and_prepare_at<P, R, NT>(reinterpret_cast<uint64_t*>(smem),
+  return load_and_prepare_at<P, R, NT, D>(reinterpret_cast<uint64_t*>(smem),
                                        reinterpret_cast<double*>(smem + LY::stage_off),
                                        reinterpret_cast<R*>(smem + LY::slab_off), mom, nevt, kp, status);
 }
 
 // ---------------------------------------------------------------------------
-// |M|^2 with the CUDA-core colour sum (FP64 path; small processes in mixed)
+// |M|^2 with the CUDA-core colour sum (FP64 path; small processes in mixed;
+// the all-float mode with D = A = float: FP32 set-up and helicity sum)
 // ---------------------------------------------------------------------------
-template <class P, typename R, int NT>
+template <class P, typename R, int NT, typename D = double, typename A = double>
 __global__ void __launch_bounds__(NT) sigma_kernel(const double* __restrict__ mom, long long nevt,
                                                    double* __restrict__ me, const int* __restrict__ hels,
                                                    int nhel, KParams kp, unsigned* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem[];
   using LY = Layout<P, R, NT>;
-  const int nvalid = load_and_prepare<P, R, NT>(smem, mom, nevt, kp, status);
+  const int nvalid = load_and_prepare<P, R, NT, D>(smem, mom, nevt, kp, status);
   if (nvalid < 0) return;
   const R* ev = reinterpret_cast<const R*>(smem + LY::slab_off) + threadIdx.x;
   cx<R>* jamp = reinterpret_cast<cx<R>*>(smem + LY::jamp_off) + threadIdx.x;
-  double acc = 0.0;
+  A acc = A(0);
 #pragma unroll 1
   for (int ih = 0; ih < nhel; ih++) {
     const int h = __ldg(hels + ih);
     P::template amplitudes<R>(ev, NT, h, kp.v, jamp, NT);
-    acc += (double)P::template colour_quadratic<R>(jamp, NT);
+    acc += (A)P::template colour_quadratic<R>(jamp, NT);
   }
   if ((int)threadIdx.x < nvalid) {
     constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
-    me[(long long)blockIdx.x * NT + threadIdx.x] = acc * norm;
+    me[(long long)blockIdx.x * NT + threadIdx.x] = (double)(acc * A(norm));
   }
 }
 
@@ -355,15 +357,15 @@ inline cudaError_t set_smem_attr(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <class P, typename R, int NT>
+template <class P, typename R, int NT, typename D = double, typename A = double>
 int launch_sigma(const LaunchArgs& a) {
   constexpr size_t smem = Layout<P, R, NT>::base_bytes;
-  static const cudaError_t attr = set_smem_attr(sigma_kernel<P, R, NT>, smem);
+  static const cudaError_t attr = set_smem_attr(sigma_kernel<P, R, NT, D, A>, smem);
   if (attr != cudaSuccess) return -4;
   if (a.nevt <= 0) return 0;  // attribute set-up only
   const long long grid = (a.nevt + NT - 1) / NT;
-  sigma_kernel<P, R, NT><<<(unsigned)grid, NT, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels, a.nhel, a.kp,
-                                                                  a.status);
+  sigma_kernel<P, R, NT, D, A><<<(unsigned)grid, NT, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels, a.nhel,
+                                                                        a.kp, a.status);
   return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
@@ -417,6 +419,7 @@ struct ProcDesc {
   int (*select_fp64)(const LaunchArgs&);
   int (*select_mixed)(const LaunchArgs&);
   int (*sigma_paper)(const LaunchArgs&);
+  int (*sigma_float)(const LaunchArgs&);  // all-float mode
 };
 
 }  // namespace mg

@@ -97,7 +97,9 @@ extern "C" int mg_process_create(const char* proc, const mg_params* p, mg_proces
   if (!proc || !p) return MG_ERR_ARG;
   const ProcDesc* d = mg::find_process(proc);
   if (!d) return MG_ERR_PROC;
-  if (p->precision != MG_FP64 && p->precision != MG_MIXED && p->precision != MG_MIXED_PAPER) return MG_ERR_ARG;
+  if (p->precision != MG_FP64 && p->precision != MG_MIXED && p->precision != MG_MIXED_PAPER &&
+      p->precision != MG_FLOAT)
+    return MG_ERR_ARG;
   KParams kp;
   int rc = make_kparams(d, *p, kp);
   if (rc) return rc;
@@ -160,7 +162,7 @@ extern "C" int mg_process_create(const char* proc, const mg_params* p, mg_proces
   LaunchArgs a{};
   a.nevt = 0;
   if (d->sigma_fp64(a) || d->sigma_mixed(a) || d->helicities(a) || d->select_fp64(a) || d->select_mixed(a) ||
-      d->sigma_paper(a)) {
+      d->sigma_paper(a) || d->sigma_float(a)) {
     mg_process_destroy(h);
     return MG_ERR_CUDA;
   }
@@ -204,6 +206,7 @@ int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, 
   a.stream = stream;
   const int rc = h->par.precision == MG_MIXED         ? h->d->sigma_mixed(a)
                  : h->par.precision == MG_MIXED_PAPER ? h->d->sigma_paper(a)
+                 : h->par.precision == MG_FLOAT       ? h->d->sigma_float(a)
                                                       : h->d->sigma_fp64(a);
   return rc ? MG_ERR_CUDA : MG_OK;
 }
@@ -238,7 +241,8 @@ extern "C" int mg_sigma_select(mg_process* h, const double* momenta_dev, int64_t
   a.col_out = col_out_dev;
   a.colw_out = colw_out_dev;
   // the paper-style mode chooses from its FP64 amplitudes
-  const int rc = (h->par.precision == MG_MIXED) ? h->d->select_mixed(a) : h->d->select_fp64(a);
+  const bool fp32 = h->par.precision == MG_MIXED || h->par.precision == MG_FLOAT;
+  const int rc = fp32 ? h->d->select_mixed(a) : h->d->select_fp64(a);
   return rc ? MG_ERR_CUDA : MG_OK;
 }
 

@@ -224,25 +224,27 @@ __device__ __forceinline__ Sp<R> ext_vbar(const FermIngr<R>& f, int lam) {
   return s;
 }
 
-// Per-event fermion ingredients in FP64 (stable forms: E - |p| = m^2/(E+|p|),
-// |p| + pz = pT^2/(|p| - pz) for pz < 0).
-__device__ __forceinline__ void fermion_ingredients(const double p[4], double m, double out[5]) {
-  const double pt2 = p[1] * p[1] + p[2] * p[2];
-  const double P = sqrt(pt2 + p[3] * p[3]);
-  const double E = p[0];
-  const double om_p = sqrt(E + P);
-  const double om_m = (m == 0.0) ? 0.0 : sqrt(m * m / (E + P));
-  const double s = (p[3] >= 0.0) ? (P + p[3]) : (pt2 / (P - p[3]));
-  double a, bre, bim;
-  if (s > 0.0) {
-    a = sqrt(s / (2.0 * P));
-    const double r = 1.0 / sqrt(2.0 * P * s);
+// Per-event fermion ingredients in the set-up precision D (FP64, or FP32 in
+// the all-float mode); stable forms: E - |p| = m^2/(E+|p|),
+// |p| + pz = pT^2/(|p| - pz) for pz < 0.
+template <typename D>
+__device__ __forceinline__ void fermion_ingredients(const D p[4], D m, D out[5]) {
+  const D pt2 = p[1] * p[1] + p[2] * p[2];
+  const D P = sqrt(pt2 + p[3] * p[3]);
+  const D E = p[0];
+  const D om_p = sqrt(E + P);
+  const D om_m = (m == D(0.0)) ? D(0.0) : sqrt(m * m / (E + P));
+  const D s = (p[3] >= D(0.0)) ? (P + p[3]) : (pt2 / (P - p[3]));
+  D a, bre, bim;
+  if (s > D(0.0)) {
+    a = sqrt(s / (D(2.0) * P));
+    const D r = D(1.0) / sqrt(D(2.0) * P * s);
     bre = p[1] * r;
     bim = p[2] * r;
   } else {
-    a = 0.0;
-    bre = 1.0;
-    bim = 0.0;
+    a = D(0.0);
+    bre = D(1.0);
+    bim = D(0.0);
   }
   out[0] = a;
   out[1] = bre;
@@ -251,30 +253,32 @@ __device__ __forceinline__ void fermion_ingredients(const double p[4], double m,
   out[4] = om_p;
 }
 
-// Per-event transverse basis e1/sqrt2, e2/sqrt2 of a massless vector (FP64).
-__device__ __forceinline__ void vector_basis(const double k[4], double out[6]) {
-  const double pt2 = k[1] * k[1] + k[2] * k[2];
-  const double P = sqrt(pt2 + k[3] * k[3]);
-  double cph, sph, cth, sth;
-  if (pt2 > 0.0) {
-    const double pt = sqrt(pt2);
+// Per-event transverse basis e1/sqrt2, e2/sqrt2 of a massless vector (set-up
+// precision D).
+template <typename D>
+__device__ __forceinline__ void vector_basis(const D k[4], D out[6]) {
+  const D pt2 = k[1] * k[1] + k[2] * k[2];
+  const D P = sqrt(pt2 + k[3] * k[3]);
+  D cph, sph, cth, sth;
+  if (pt2 > D(0.0)) {
+    const D pt = sqrt(pt2);
     cph = k[1] / pt;
     sph = k[2] / pt;
     cth = k[3] / P;
     sth = pt / P;
   } else {
-    cph = 1.0;
-    sph = 0.0;
-    cth = (k[3] >= 0.0) ? 1.0 : -1.0;
-    sth = 0.0;
+    cph = D(1.0);
+    sph = D(0.0);
+    cth = (k[3] >= D(0.0)) ? D(1.0) : -D(1.0);
+    sth = D(0.0);
   }
-  const double r = 0.70710678118654752440;
+  const D r = D(0.70710678118654752440);
   out[0] = r * cth * cph;
   out[1] = r * cth * sph;
   out[2] = -r * sth;
   out[3] = -r * sph;
   out[4] = r * cph;
-  out[5] = 0.0;
+  out[5] = D(0.0);
 }
 
 // Same ingredients in the compute precision R, from a momentum in R: used by

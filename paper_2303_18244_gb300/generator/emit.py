@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import math
 import os
+import re
 
 from .colour import colour_matrix_exact, common_denominator, words
 from .diagrams import build_plan, count_diagrams
@@ -987,12 +988,39 @@ def emit(proc: str) -> tuple[str, str]:
     """(tag, header source) for a process string."""
     tag, n = PROCESSES[proc]
     if tag == "eemumu":
-        return tag, emit_eemumu(tag)
-    if tag == "uutt":
-        return tag, emit_uutt(tag)
-    if tag == "uuttg":
-        return tag, emit_uuttg(tag)
-    return tag, emit_gg(n, tag, mode="chunked" if tag in CHUNKED else "straight")
+        src = emit_eemumu(tag)
+    elif tag == "uutt":
+        src = emit_uutt(tag)
+    elif tag == "uuttg":
+        src = emit_uuttg(tag)
+    else:
+        src = emit_gg(n, tag, mode="chunked" if tag in CHUNKED else "straight")
+    return tag, _prepare_in_D(src)
+
+
+def _prepare_in_D(src: str) -> str:
+    """Give prepare() a second template parameter D, the arithmetic type of the
+    per-event set-up (double by default; float for the all-FP32 mode): the
+    emitted FP64 set-up is rewritten with D for double, the event's momenta
+    converted to D once."""
+    head = "template <typename R>\n__device__ static __forceinline__ void prepare("
+    assert src.count(head) == 1
+    src = src.replace(head, "template <typename R, typename D = double>\n"
+                            "__device__ static __forceinline__ void prepare(", 1)
+    lines = src.split("\n")
+    i0 = next(i for i, l in enumerate(lines) if "void prepare(" in l)
+    i1 = next(i for i in range(i0, len(lines)) if lines[i].rstrip().endswith("const int es) {"))
+    i2 = next(i for i in range(i1, len(lines)) if lines[i] == "}")
+    body = ["  D pd[NPAR * 4];", "  for (int i = 0; i < NPAR * 4; i++) pd[i] = D(p[i]);"]
+    for l in lines[i1 + 1:i2]:
+        if not l.startswith("#"):
+            l = re.sub(r"\bdouble\b", "D", l)
+            l = re.sub(r"(?<![\w.])p\[", "pd[", l)
+            l = l.replace("(p + ", "(pd + ")
+            l = re.sub(r"\bkp\[(\d)\]", r"D(kp[\1])", l)
+            l = re.sub(r"(?<![\w.\[])(\d+\.\d+)(?![\w.])", r"D(\1)", l)
+        body.append(l)
+    return "\n".join(lines[:i1 + 1] + body + lines[i2:])
 
 
 # threads per CTA: FP64 path / mixed path (shared-memory slab sizes differ)
@@ -1058,6 +1086,7 @@ def emit_tu(proc: str, prec: str) -> tuple[str, str]:
 namespace mg {{
 int sigma_{tag}_mixed(const LaunchArgs& a) {{ return {mixed}; }}
 int select_{tag}_mixed(const LaunchArgs& a) {{ return launch_select<{tag}, float, {nt32}>(a); }}
+int sigma_{tag}_float(const LaunchArgs& a) {{ return launch_sigma<{tag}, float, {nt32}, float, float>(a); }}
 }}  // namespace mg
 """
         return tag, src
@@ -1073,11 +1102,12 @@ static int select_fp64(const LaunchArgs& a) {{ return launch_select<{tag}, doubl
 static int paper(const LaunchArgs& a) {{ return launch_sigma_paper<{tag}, {nt64}>(a); }}
 int sigma_{tag}_mixed(const LaunchArgs& a);
 int select_{tag}_mixed(const LaunchArgs& a);
+int sigma_{tag}_float(const LaunchArgs& a);
 static_assert({tag}::NCOL == {ncol}, "colour-flow count");
 static const ProcDesc desc = {{"{proc}", "{tag}", {tag}::NPAR, {tag}::NHEL, {tag}::NCOL, {tag}::NDIAG,
                               {tag}::NAMP, {tag}::IDEN, {tag}::CDEN, {tag}::KNUM,
                               sigma_fp64, sigma_{tag}_mixed, helicities, {tck},
-                              select_fp64, select_{tag}_mixed, paper}};
+                              select_fp64, select_{tag}_mixed, paper, sigma_{tag}_float}};
 const ProcDesc* proc_{tag}() {{ return &desc; }}
 }}  // namespace mg
 """

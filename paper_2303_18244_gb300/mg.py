@@ -21,6 +21,7 @@ MG_PENDING = 1
 MG_FP64 = 0
 MG_MIXED = 1
 MG_MIXED_PAPER = 2
+MG_FLOAT = 3
 MG_NO_TOP_WIDTH = 1
 MG_PHOTON_ONLY = 2
 

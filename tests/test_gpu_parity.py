@@ -282,3 +282,23 @@ def test_paper_mixed_parity_small(proc):
     got = _gpu_me(h, p)
     r = _rel(got, O.me(proc, p))
     assert np.median(r) <= 1e-6 and r.max() <= 1e-4
+
+
+@pytest.mark.parametrize("proc", PROCS, ids=_ids)
+def test_float_parity_small(proc):
+    """The paper's float mode: every step in FP32, including the per-event
+    set-up and the propagator denominators.  Bounds: FP32 rounding (6e-8)
+    grows with the number of terms (up to ~1e5 per helicity) and with the
+    cancellation in P^2 - m^2 near the top mass shell (|P^2| / |P^2 - m^2| up
+    to ~1e3 for soft gluons off a top), so single events can lose several
+    digits; the typical event keeps about six."""
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, n, _ = WORKLOADS[proc]
+    p = process_momenta(proc, rs, n, seed)
+    h = mg.Process(proc, precision=mg.MG_FLOAT)
+    got = _gpu_me(h, p)
+    r = _rel(got, O.me(proc, p))
+    print(f"{proc}: float rel err median {np.median(r):.2e} p99 {np.quantile(r, 0.99):.2e} max {r.max():.2e}")
+    assert np.all(np.isfinite(got))
+    assert np.median(r) <= 1e-5 and np.quantile(r, 0.99) <= 1e-3 and r.max() <= 5e-2
