@@ -19,6 +19,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 // MG_VERTEX: inlining of the vertex routines (ffv_*, vvv_*, vvvv_*).  Inlined
 // by default; a translation unit may define it as __noinline__, which turns a
 // large process's straight-line helicity program into a sequence of calls to

@@ -344,8 +344,17 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
                 curc = []
         if curc:
             chunks.append(curc)
-        # pass 1: where each current is produced and which later chunks read it
-        local_kinds = ("ext", "ubar", "v")
+        # pass 1: where each current is produced and which later chunks read it.
+        # Local currents are recomputed in every chunk that uses them instead
+        # of passing through the store: the external states, and with
+        # MG_REMAT=1 also the currents built from external states only.
+        remat = os.environ.get("MG_REMAT", "0") == "1"
+        ext_kinds = ("ext", "ubar", "v")
+
+        def is_local(c):
+            if plan.ops[c][0] in ext_kinds:
+                return True
+            return remat and all(plan.ops[d][0] in ext_kinds for d in current_deps(plan, c))
         produced, readers = {}, {}
         for j, ch in enumerate(chunks):
             seen = set()
@@ -354,12 +363,12 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
                 if c in seen:
                     return
                 seen.add(c)
-                if plan.ops[c][0] not in local_kinds and c in produced:
+                if not is_local(c) and c in produced:
                     readers.setdefault(c, set()).add(j)
                     return
                 for d in current_deps(plan, c):
                     visit(d)
-                if plan.ops[c][0] not in local_kinds:
+                if not is_local(c):
                     produced[c] = j
             for ai in ch:
                 for d in amp_deps(plan, plan.amps[ai][0]):
@@ -1011,7 +1020,12 @@ def _prepare_in_D(src: str) -> str:
     i0 = next(i for i, l in enumerate(lines) if "void prepare(" in l)
     i1 = next(i for i in range(i0, len(lines)) if lines[i].rstrip().endswith("const int es) {"))
     i2 = next(i for i in range(i1, len(lines)) if lines[i] == "}")
-    body = ["  D pd[NPAR * 4];", "  for (int i = 0; i < NPAR * 4; i++) pd[i] = D(p[i]);"]
+    # E: arithmetic type of the external-state ingredients (spinor and
+    # polarisation set-up), FP32 whenever the amplitudes are FP32; the
+    # propagator denominators keep D
+    body = ["  D pd[NPAR * 4];", "  for (int i = 0; i < NPAR * 4; i++) pd[i] = D(p[i]);",
+            "  using E = typename std::conditional<sizeof(R) == 4, float, D>::type;",
+            "  E pe[NPAR * 4];", "  for (int i = 0; i < NPAR * 4; i++) pe[i] = E(p[i]);"]
     for l in lines[i1 + 1:i2]:
         if not l.startswith("#"):
             l = re.sub(r"\bdouble\b", "D", l)
@@ -1019,6 +1033,12 @@ def _prepare_in_D(src: str) -> str:
             l = l.replace("(p + ", "(pd + ")
             l = re.sub(r"\bkp\[(\d)\]", r"D(kp[\1])", l)
             l = re.sub(r"(?<![\w.\[])(\d+\.\d+)(?![\w.])", r"D(\1)", l)
+            if "vector_basis(" in l:
+                l = l.replace("D b[6]", "E b[6]").replace("vector_basis(pd", "vector_basis(pe")
+            if "fermion_ingredients(" in l:
+                l = l.replace("D f[5]", "E f[5]")
+                l = re.sub(r"fermion_ingredients\(pd( \+ [^,]+), ([^;]+), f\);",
+                           r"fermion_ingredients(pe\1, E(\2), f);", l)
         body.append(l)
     return "\n".join(lines[:i1 + 1] + body + lines[i2:])
 
@@ -1051,9 +1071,10 @@ TENSOR_CORE_ROWS = set(filter(None, os.environ.get("MG_TC_ROWS", "ggttggg").spli
 # precision: the straight-line helicity program then shrinks to a sequence of
 # calls to a few small routines that stay in the instruction cache.  Measured:
 # faster for the FP32 path of the larger processes, whose inlined program
-# streams from L2 on every helicity; the FP64 path of gg -> t t~ g g (bound by
-# the FP64 pipe) and the smaller processes keep the inlined code
-VERTEX_CALLS = {"f32": {"ggttgg", "ggttggg"}, "f64": {"ggttggg"}}
+# streams from L2 on every helicity; the FP64 paths (bound by the FP64 pipe;
+# gg -> t t~ g g g 1.05e4 inlined against 8.4e3 called) and the smaller
+# processes keep the inlined code
+VERTEX_CALLS = {"f32": {"ggttgg", "ggttggg"}, "f64": set()}
 
 
 # colour-flow counts of the processes written by hand (gg processes: n!)
