@@ -130,8 +130,10 @@ def load_flops(tag: str) -> dict:
         return json.load(f)[tag]
 
 
-def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: float = 12.0):
-    """FP64 oracle on the host cores over a bounded sample: (MEs/s, cores, n)."""
+def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: float = 12.0,
+                one_core: bool = True):
+    """FP64 oracle on the host cores over a bounded sample of the workload's
+    first events: (MEs/s, cores, n, seconds, MEs/s on one core, oracle values)."""
     import oracle as O
     from paper_2303_18244_gb300.inputs import process_momenta
     cores = os.cpu_count() or 1
@@ -141,13 +143,19 @@ def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: 
     while True:
         p = process_momenta(proc, sqrts, n, seed, first_event)
         t = time.perf_counter()
-        O.me(proc, p, threads=cores)
+        ref = O.me(proc, p, threads=cores)
         dt = time.perf_counter() - t
         best = (n / dt, cores, n, dt)
         if dt >= budget_s / 4 or n >= 1 << 20:
             break
         n = int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3))))
-    return best
+    one = None
+    if one_core:  # one core, on a sample about two seconds long
+        n1 = max(1, min(n, int(best[0] / cores * 2.0)))
+        t = time.perf_counter()
+        O.me(proc, p[:n1], threads=1)
+        one = n1 / (time.perf_counter() - t)
+    return best + (one, ref)
 
 
 def run_reference(args):
@@ -158,9 +166,9 @@ def run_reference(args):
     vals = []
     info = None
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        time_oracle(PROC, SQRTS, SEED, 0, budget_s=2.0)
+        time_oracle(PROC, SQRTS, SEED, 0, budget_s=2.0, one_core=False)
     for _ in range(args.steps):
-        v, cores, n, dt = time_oracle(PROC, SQRTS, SEED, 0, budget_s=8.0)
+        v, cores, n, dt, _, _ = time_oracle(PROC, SQRTS, SEED, 0, budget_s=8.0, one_core=False)
         vals.append(v)
         info = (cores, n)
     v = statistics.median(vals)
@@ -290,6 +298,25 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_t = max_over_ranks([statistics.median(e2e_ms)], device="cuda")[0]
 
+    # the same with the phase-space points generated on the device (mg_rambo,
+    # the paper's proposed offload of the random-number -> momenta step):
+    # only the MEs cross to the host
+    dmom = torch.empty_like(mom)
+    for _ in range(2):
+        mg.rambo(hmix, SQRTS, SEED, first, dmom, stream)
+        mg.sigma(hmix, dmom, out, stream)
+    torch.cuda.synchronize()
+    dev_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mg.rambo(hmix, SQRTS, SEED, first, dmom, stream)
+        mg.sigma(hmix, dmom, out, stream)
+        ho.copy_(out)  # D2H of the MEs (synchronous)
+        dev_ms.append((time.perf_counter() - t0) * 1e3)
+    dev_t = max_over_ranks([statistics.median(dev_ms)], device="cuda")[0]
+
     fl = load_flops(args.proc)
     flops_evt = ngood * (fl["amp_flops_per_hel"] + fl["colour_dense_flops_per_hel"])
     kernel_ms = t_mix / args.steps
@@ -322,6 +349,9 @@ def main():
                                    "max": float(rel.max()), "events": nevt},
         "e2e": {"value": world * nevt / (e2e_t * 1e-3), "unit": "MEs/s",
                 "h2d_bytes_per_step": int(p.nbytes), "d2h_bytes_per_step": int(nevt * 8)},
+        "e2e_device_phase_space": {"value": world * nevt / (dev_t * 1e-3), "unit": "MEs/s",
+                                   "what": "mg_rambo + mg_sigma + D2H of the MEs per step",
+                                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(nevt * 8)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                      "frac": achieved / peak32, "traffic": traffic,
                      "kernel": f"sigma kernel of {args.proc}, mixed",
@@ -331,9 +361,17 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, n, dt = time_oracle(PROC, SQRTS, SEED, first)
+        v, cores, n, dt, one, ref = time_oracle(PROC, SQRTS, SEED, first)
         res["cpu_baseline"] = {"value": v, "unit": "MEs/s", "cores": cores, "kind": "oracle",
-                               "sample": f"{n} events of the workload ({dt:.1f} s wall)"}
+                               "sample": f"the first {n} events of the workload ({dt:.1f} s wall)",
+                               "value_one_core": one}
+        # per-event relative error of both GPU paths against the oracle on that sample
+        acc = {}
+        for name, o in (("fp64", out64), ("mixed", out)):
+            r = np.abs(o[:n].cpu().numpy() - ref) / np.abs(ref)
+            acc[name] = {"median": float(np.median(r)), "p99": float(np.quantile(r, 0.99)),
+                         "max": float(r.max()), "events": int(n)}
+        res["accuracy_vs_oracle"] = acc
     if not args.no_serve and args.proc == "ggttgg":
         nreq = args.serve_requests or (2000 if args.serve else 120)
         plan = {"mixed": nreq, "fp64": max(1, nreq // 10)} if args.serve else {"mixed": nreq}

@@ -347,7 +347,8 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         # pass 1: where each current is produced and which later chunks read it.
         # Local currents are recomputed in every chunk that uses them instead
         # of passing through the store: the external states, and with
-        # MG_REMAT=1 also the currents built from external states only.
+        # MG_REMAT=1 also the currents built from external states only
+        # (gg -> t t~ g g g: measured 6 % slower in FP32, 17 % in FP64).
         remat = os.environ.get("MG_REMAT", "0") == "1"
         ext_kinds = ("ext", "ubar", "v")
 
