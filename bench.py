@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # kernel from one ncu capture of the current kernel on a small case: workload
 # -> (events captured, bytes); scaled to a launch by its events (the traffic
 # is per event: momenta in, |M|^2 out).  Set to None when the kernel changes.
-NCU_TRAFFIC = {"ggttgg": (65536, 12.798720e6 + 9.216e3)}  # sigma_tc_kernel_ggttgg_mixed_65536ev.md (D)
+NCU_TRAFFIC = {"ggttgg": None}  # set from the capture of the current kernel
 
 SERVE_PROCS = {  # process -> sqrt(s)
     "e+ e- > mu+ mu-": 500.0,
@@ -128,6 +128,18 @@ class ClockSampler:
 def load_flops(tag: str) -> dict:
     with open(os.path.join(ROOT, "paper_2303_18244_gb300", "flops.json")) as f:
         return json.load(f)[tag]
+
+
+def launches_per_sigma(proc: str, nevt: int, ngood: int) -> int:
+    """Kernel launches of one mixed mg_sigma call: one, except for gg -> t t~ g g g,
+    whose two-phase path launches the flow and colour kernels once per slice
+    of the good helicities, the slices sized to a 1 GiB flow workspace
+    (120 complex FP32 flows per helicity-event row, events padded to 128)."""
+    if proc != "ggttggg":
+        return 1
+    per_hel = 120 * ((nevt + 127) // 128 * 128) * 8
+    hs = max(1, min(ngood, (1 << 30) // per_hel))
+    return 2 * ((ngood + hs - 1) // hs)
 
 
 def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: float = 12.0,
@@ -357,7 +369,7 @@ def main():
                      "kernel": f"sigma kernel of {args.proc}, mixed",
                      "flops_per_event": flops_evt,
                      "peak_source": "measured FP32 FMA loop (mg_diag), burst"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_sigma(args.proc, nevt, ngood),
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -368,9 +380,22 @@ def main():
         # per-event relative error of both GPU paths against the oracle on that sample
         acc = {}
         for name, o in (("fp64", out64), ("mixed", out)):
-            r = np.abs(o[:n].cpu().numpy() - ref) / np.abs(ref)
+            got = o[:n].cpu().numpy()
+            r = np.abs(got - ref) / np.abs(ref)
             acc[name] = {"median": float(np.median(r)), "p99": float(np.quantile(r, 0.99)),
                          "max": float(r.max()), "events": int(n)}
+            if name == "fp64":
+                # where the FP64 oracle and the FP64 path differ by more than
+                # 1e-12, the oracle's long-double build decides
+                import oracle as O
+                bad = np.nonzero(r > 1e-12)[0]
+                r_adj = r.copy()
+                if bad.size:
+                    pb = process_momenta(PROC, SQRTS, n, SEED, first_event=first)[bad]
+                    ext = O.me(PROC, pb, extended=True)
+                    r_adj[bad] = np.abs(got[bad] - ext) / np.abs(ext)
+                acc[name]["beyond_1e-12"] = int(bad.size)
+                acc[name]["max_adjudicated"] = float(r_adj.max())
         res["accuracy_vs_oracle"] = acc
     if not args.no_serve and args.proc == "ggttgg":
         nreq = args.serve_requests or (2000 if args.serve else 120)
