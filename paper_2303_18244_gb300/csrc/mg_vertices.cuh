@@ -283,6 +283,56 @@ __device__ __forceinline__ void vector_basis(const D k[4], D out[6]) {
   out[5] = D(0.0);
 }
 
+// Minkowski square of a signed sum of four-vectors minus m2,
+//   (sum_n s_n v_n)^2 - m2,   s_n = +-1.
+// In the FP64 path (R and D double) every component sum and square is carried
+// as an unevaluated sum of two doubles (Knuth's error-free two-sum, and the
+// product error from an FMA): the invariant of nearly collinear momenta, or of
+// a nearly on-shell top, then keeps full relative precision instead of losing
+// the digits of its cancellation.  Elsewhere it is the plain formula in D.
+template <typename D>
+__host__ __device__ __forceinline__ void two_sum(D a, D b, D& s, D& e) {
+  s = a + b;
+  const D bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+template <typename R, typename D, int N>
+__device__ __forceinline__ D inv_mass2(const D* const (&v)[N], const D (&s)[N], D m2) {
+  if constexpr (sizeof(R) == 8 && sizeof(D) == 8) {
+    D hi = -m2, lo = D(0);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      D ch = s[0] * v[0][mu], cl = D(0);
+#pragma unroll
+      for (int k = 1; k < N; k++) {
+        D e;
+        two_sum(ch, s[k] * v[k][mu], ch, e);
+        cl += e;
+      }
+      const D sq = ch * ch;
+      const D sq_lo = ::fma(ch, ch, -sq) + D(2) * ch * cl;
+      D e;
+      if (mu == 0) {
+        two_sum(hi, sq, hi, e);
+        lo += e + sq_lo;
+      } else {
+        two_sum(hi, -sq, hi, e);
+        lo += e - sq_lo;
+      }
+    }
+    return hi + lo;
+  } else {
+    D c[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      c[mu] = s[0] * v[0][mu];
+#pragma unroll
+      for (int k = 1; k < N; k++) c[mu] = c[mu] + s[k] * v[k][mu];
+    }
+    return c[0] * c[0] - c[1] * c[1] - c[2] * c[2] - c[3] * c[3] - m2;
+  }
+}
+
 // Same ingredients in the compute precision R, from a momentum in R: used by
 // the FP32 path, which recomputes them per helicity instead of keeping them in
 // shared memory (a few flops against tens of thousands per helicity).

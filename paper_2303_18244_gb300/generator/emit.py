@@ -173,26 +173,30 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             L.append(f"    EV({sl[fname] + j}) = R(f[{j}]);")
         L.append("  }")
 
-    def ksum_fp64(mask):
-        idx = [i for i in range(n) if mask >> i & 1]
-        return [" + ".join(f"k{i}[{mu}]" for i in idx) for mu in range(4)]
+    # propagator invariants: (sum of the momenta)^2 [- m^2] by inv_mass2,
+    # compensated (double-double) in the FP64 path, so that a nearly collinear
+    # or nearly on-shell propagator keeps full relative precision
+    def inv_mass2(rows, m2):
+        vv = ", ".join(v for v, _ in rows)
+        ss = ", ".join("double(1)" if sg > 0 else "double(-1)" for _, sg in rows)
+        return (f"const double* const vv[{len(rows)}] = {{{vv}}}; const double ss[{len(rows)}] = {{{ss}}};",
+                f"inv_mass2<R>(vv, ss, {m2})")
 
     for m in gmasks:
-        comps = ksum_fp64(m)
-        L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
-        L.append("    const double P2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];")
+        decl, call = inv_mass2([(f"k{i}", 1) for i in range(n) if m >> i & 1], "0.0")
+        L.append(f"  {{ {decl}")
+        L.append(f"    const double P2 = {call};")
         L.append(f"    EV({sl[f'cg{m}']}) = R(-g / P2); }}")
     for m in fmasks:
-        comps = ksum_fp64(m) if m else ["0.0"] * 4
-        L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
-        L.append("    double Q[4]; for (int mu = 0; mu < 4; mu++) Q[mu] = p[8 + mu] - K[mu];")
-        L.append("    const double dre = Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3] - mt * mt;")
+        decl, call = inv_mass2([("pd + 8", 1)] + [(f"k{i}", -1) for i in range(n) if m >> i & 1], "mt * mt")
+        L.append(f"  {{ {decl}")
+        L.append(f"    const double dre = {call};")
         L.append("    const double dim = mt * wt;")
         L.append("    const double r = -g / (dre * dre + dim * dim);")
         L.append(f"    EV({sl[f'cf{m}']}) = R(r * dre); EV({sl[f'cf{m}'] + 1}) = R(-r * dim); }}")
-    comps = ksum_fp64(full)
-    L.append(f"  {{ const double K[4] = {{{', '.join(comps)}}};")
-    L.append("    const double P2 = K[0] * K[0] - K[1] * K[1] - K[2] * K[2] - K[3] * K[3];")
+    decl, call = inv_mass2([(f"k{i}", 1) for i in range(n)], "0.0")
+    L.append(f"  {{ {decl}")
+    L.append(f"    const double P2 = {call};")
     L.append(f"    EV({sl['cgtt']}) = R(g / P2); }}")
     L.append("#undef EV")
     L.append("}")
@@ -296,12 +300,12 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     for ai in amp_order:
         last_of[pid[ai]] = ai
 
-    # straight-line mode: a (row, column) spinor pair used by several top-line
-    # amplitudes is contracted once into V = rbar gamma^mu c, and each of its
-    # amplitudes becomes the Minkowski product V.J (gg -> t t~ g g: 74 pairs
-    # for 114 amplitudes; measured 6 % faster in FP32, 11 % in FP64;
-    # MG_PAIR_V=0 turns it off)
-    pair_v = mode == "straight" and os.environ.get("MG_PAIR_V", "1") == "1"
+    # a (row, column) spinor pair used by several top-line amplitudes (of the
+    # program, or of one chunk in chunked mode) is contracted once into
+    # V = rbar gamma^mu c, and each of its amplitudes becomes the Minkowski
+    # product V.J (gg -> t t~ g g: 74 pairs for 114 amplitudes, measured 6 %
+    # faster in FP32, 11 % in FP64; MG_PAIR_V=0 turns it off)
+    pair_v = os.environ.get("MG_PAIR_V", "1") == "1"
     pair_uses: dict = {}
     for ai in amp_order:
         op = plan.amps[ai][0]
@@ -423,6 +427,12 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             for i in range(npar):
                 L.append(f"  const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
             L.append("  cx<R> pacc = {R(0), R(0)};")
+            pair_names.clear()
+            pair_uses.clear()
+            for ai in ch:
+                op = plan.amps[ai][0]
+                if op[0] == "f":
+                    pair_uses[(op[1], op[3])] = pair_uses.get((op[1], op[3]), 0) + 1
             for ai in ch:
                 emit_amp(ai)
             for c in sorted(cross):
@@ -935,12 +945,19 @@ def emit_uuttg(tag: str) -> str:
     L.append("  }")
     L.append("  for (int k = 0; k < 6; k++)")
     L.append("    for (int mu = 0; mu < 4; mu++) EV(26 + 4 * k + mu) = R(q[k][mu]);")
+    L.append("  // invariants compensated in the FP64 path (inv_mass2): collinear emissions")
     L.append("  double m2[6];")
-    L.append("  for (int k = 0; k < 6; k++) m2[k] = q[k][0] * q[k][0] - q[k][1] * q[k][1] - q[k][2] * q[k][2] - q[k][3] * q[k][3];")
+    rows = [[("pd + 0", 1), ("pd + 16", -1)], [("pd + 16", 1), ("pd + 4", -1)], [("pd + 8", 1), ("pd + 16", 1)],
+            [("pd + 12", -1), ("pd + 16", -1)], [("pd + 0", 1), ("pd + 4", 1)], [("pd + 8", -1), ("pd + 12", -1)]]
+    for k, rr in enumerate(rows):
+        vv = ", ".join(v for v, _ in rr)
+        ss = ", ".join("double(1)" if sg > 0 else "double(-1)" for _, sg in rr)
+        L.append(f"  {{ const double* const vv[2] = {{{vv}}}; const double ss[2] = {{{ss}}};")
+        L.append(f"    m2[{k}] = inv_mass2<R>(vv, ss, {'mt * mt' if k in (2, 3) else '0.0'}); }}")
     L.append("  EV(50) = R(-g / m2[0]);")
     L.append("  EV(51) = R(-g / m2[1]);")
     L.append("  for (int k = 2; k < 4; k++) {")
-    L.append("    const double dre = m2[k] - mt * mt, dim = mt * wt, r = -g / (dre * dre + dim * dim);")
+    L.append("    const double dre = m2[k], dim = mt * wt, r = -g / (dre * dre + dim * dim);  // m2[2], m2[3]: q^2 - mt^2")
     L.append("    EV(52 + 2 * (k - 2)) = R(r * dre); EV(53 + 2 * (k - 2)) = R(-r * dim);")
     L.append("  }")
     L.append("  EV(56) = R(1.0 / m2[5]);")

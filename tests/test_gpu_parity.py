@@ -302,3 +302,19 @@ def test_float_parity_small(proc):
     print(f"{proc}: float rel err median {np.median(r):.2e} p99 {np.quantile(r, 0.99):.2e} max {r.max():.2e}")
     assert np.all(np.isfinite(got))
     assert np.median(r) <= 1e-5 and np.quantile(r, 0.99) <= 1e-3 and r.max() <= 5e-2
+
+
+def test_fp64_ill_conditioned_event_against_extended_oracle():
+    """Event 29039 of the gg -> t t~ g g workload has an initial and a final
+    gluon 0.33 GeV^2 from collinear: a t-channel invariant that cancels to six
+    digits in FP64 components.  The FP64 oracle loses them (5e-10 from its
+    long-double build); the FP64 path, whose propagator invariants are
+    compensated, must stay within 1e-12 of the long-double value on it and its
+    neighbours."""
+    proc = "g g > t t~ g g"
+    p = process_momenta(proc, 1500.0, 29040, 3)[29030:29040].copy()
+    h = mg.Process(proc)
+    got = _gpu_me(h, p)
+    ext = O.me(proc, p, extended=True)
+    assert _rel(got, ext).max() <= 1e-12
+    assert _rel(O.me(proc, p), ext).max() > 1e-10  # the FP64 oracle itself does not
