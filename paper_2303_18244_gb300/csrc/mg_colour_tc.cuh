@@ -24,6 +24,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "mg_flowstore.cuh"
 #include "mg_kernels.cuh"
 
 namespace mg {
@@ -472,6 +473,77 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// First phase with the colour flows in tensor memory (MG_FLOWS_TMEM): 128
+// events per CTA, TMEM lane = event, two columns per flow; shared memory holds
+// only the momenta tile and the per-event slab, so that two CTAs (8 warps)
+// fit on an SM instead of two CTAs of 64 events.  Same output as flows_kernel.
+#ifndef MG_FLOWS_TMEM
+#define MG_FLOWS_TMEM 0
+#endif
+template <class P>
+struct LayoutFlowsTmem {
+  static constexpr int NT = 128;
+  static constexpr size_t r128(size_t b) { return ((b + 127) / 128) * 128; }
+  static constexpr size_t bar_bytes = 128;  // TMA bar, TMEM address
+  static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
+  static constexpr size_t slab_bytes = size_t(NT) * slab_slots<P, float>() * sizeof(float);
+  static constexpr size_t stage_off = bar_bytes;
+  static constexpr size_t slab_off = stage_off + r128(stage_bytes);
+  static constexpr size_t base_bytes = slab_off + r128(slab_bytes);
+  static constexpr uint32_t tmem_cols = 256;
+};
+
+template <class P>
+__global__ void __launch_bounds__(128)
+    flows_tmem_kernel(const double* __restrict__ mom, long long nevt, float2* __restrict__ J, long long ldj,
+                      const int* __restrict__ hels, int nhel, KParams kp, unsigned* __restrict__ status) {
+  using LY = LayoutFlowsTmem<P>;
+  constexpr int NT = 128;
+  static_assert(2 * P::NCOL <= (int)LY::tmem_cols, "flows fit in the allocated columns");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+  double* stage = reinterpret_cast<double*>(smem + LY::stage_off);
+  float* slab = reinterpret_cast<float*>(smem + LY::slab_off);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int nvalid = load_and_prepare_at<P, float, NT>(tma_bar, stage, slab, mom, nevt, kp, status);
+  if (nvalid < 0) return;
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, LY::tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const FlowsTmem fl{tmem + ((uint32_t)(warp * 32) << 16)};
+  const long long e = (long long)blockIdx.x * NT + tid;
+#pragma unroll 1
+  for (int ih = 0; ih < nhel; ih++) {
+    const int h = __ldg(hels + ih);
+    P::template amplitudes_store<float>(slab + tid, NT, h, kp.v, fl);
+    float2* row = J + (long long)ih * P::NCOL * ldj + e;
+#pragma unroll 1
+    for (int c = 0; c < 2 * P::NCOL; c += 16) {
+      float v[16];
+      tc::tmem_ld16(fl.taddr + (uint32_t)c, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int k = c / 2 + q;
+        if (k < P::NCOL) row[(long long)k * ldj] = make_float2(v[2 * q], v[2 * q + 1]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, LY::tmem_cols);
+  }
+}
+
 // The two phases over slices of the good helicities, every event in each
 // launch (full grids), with a stream-ordered workspace of at most
 // ROWS_WORKSPACE bytes of flows (FP32 complex [slice][NCOL][events]).
@@ -480,9 +552,16 @@ constexpr size_t ROWS_WORKSPACE = size_t(1) << 30;
 template <class P, int NT>
 int launch_sigma_rows(const LaunchArgs& a) {
   static_assert(128 % NT == 0, "flow rows are padded to 128 events");
-  constexpr size_t smem1 = Layout<P, float, NT>::base_bytes;
+  constexpr bool tmem_flows = MG_FLOWS_TMEM != 0;
+  constexpr int NT1 = tmem_flows ? 128 : NT;
+  constexpr size_t smem1 = tmem_flows ? LayoutFlowsTmem<P>::base_bytes : Layout<P, float, NT>::base_bytes;
   constexpr size_t smem2 = LayoutRows<P>::base_bytes;
-  static const cudaError_t attr1 = set_smem_attr(flows_kernel<P, NT>, smem1);
+  static const cudaError_t attr1 = [] {
+    if constexpr (tmem_flows)
+      return set_smem_attr(flows_tmem_kernel<P>, smem1);
+    else
+      return set_smem_attr(flows_kernel<P, NT>, smem1);
+  }();
   static const cudaError_t attr2 = set_smem_attr(colour_rows_tc_kernel<P>, smem2);
   if (attr1 != cudaSuccess || attr2 != cudaSuccess) return -4;
   if (a.nevt <= 0 || a.nhel <= 0) return 0;
@@ -494,8 +573,12 @@ int launch_sigma_rows(const LaunchArgs& a) {
   if (cudaMallocAsync(reinterpret_cast<void**>(&J), (size_t)hs * per_hel, a.stream) != cudaSuccess) return -4;
   for (int h0 = 0; h0 < a.nhel; h0 += (int)hs) {
     const int nh = a.nhel - h0 < hs ? a.nhel - h0 : (int)hs;
-    flows_kernel<P, NT><<<(unsigned)((a.nevt + NT - 1) / NT), NT, smem1, a.stream>>>(
-        a.mom, a.nevt, J, ldj, a.hels + h0, nh, a.kp, a.status);
+    if constexpr (tmem_flows)
+      flows_tmem_kernel<P><<<(unsigned)((a.nevt + NT1 - 1) / NT1), NT1, smem1, a.stream>>>(
+          a.mom, a.nevt, J, ldj, a.hels + h0, nh, a.kp, a.status);
+    else
+      flows_kernel<P, NT><<<(unsigned)((a.nevt + NT - 1) / NT), NT, smem1, a.stream>>>(
+          a.mom, a.nevt, J, ldj, a.hels + h0, nh, a.kp, a.status);
     colour_rows_tc_kernel<P><<<(unsigned)(ldj / 128), 128, smem2, a.stream>>>(
         J, ldj, a.nevt, a.out, nh, h0 == 0, h0 + nh == a.nhel, static_cast<const uint4*>(a.ctile), a.status);
   }

@@ -1,0 +1,81 @@
+// mg_flowstore.cuh -- where a thread keeps its event's colour-flow
+// accumulators (JAMPs) while the chunked helicity program runs.
+//
+// The chunk functions of the largest process update the flows through one
+// of these stores: a pattern of amplitudes, summed in a register, is added to
+// (or subtracted from) each flow of the pattern at once.
+//
+//   FlowsSmem<R>  the thread's column of a [flow][thread] array in shared
+//                 memory (stride js), any precision;
+//   FlowsTmem     two columns per flow (re, im) of the thread's lane of
+//                 tensor memory (FP32), read and written with tcgen05.ld/st:
+//                 it keeps 120 complex flows per event off shared memory, so
+//                 that more events fit on an SM.  Warp-collective: every
+//                 thread of the warp must make the same calls.
+#pragma once
+
+#include "mg_vertices.cuh"
+
+namespace mg {
+
+template <typename R>
+struct FlowsSmem {
+  cx<R>* p;
+  int js;
+  template <int N>
+  __device__ __forceinline__ void update(const int (&k)[N], const int (&sg)[N], cx<R> v) const {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      cx<R>& t = p[k[i] * js];
+      t = sg[i] > 0 ? t + v : t - v;
+    }
+  }
+  __device__ __forceinline__ void zero(int n) const {
+    for (int c = 0; c < n; c++) p[c * js] = cx<R>{R(0), R(0)};
+  }
+};
+
+struct FlowsTmem {
+  uint32_t taddr;  // lane (bits 16-31) and first column of the thread's flows
+  template <int N>
+  __device__ __forceinline__ void update(const int (&k)[N], const int (&sg)[N], cx<float> v) const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();  // the tcgen05 accesses below are warp-collective
+    uint32_t r[2 * N];
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                   : "=r"(r[2 * i]), "=r"(r[2 * i + 1])
+                   : "r"(taddr + 2u * (uint32_t)k[i])
+                   : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const float re = __uint_as_float(r[2 * i]), im = __uint_as_float(r[2 * i + 1]);
+      r[2 * i] = __float_as_uint(sg[i] > 0 ? re + v.re : re - v.re);
+      r[2 * i + 1] = __float_as_uint(sg[i] > 0 ? im + v.im : im - v.im);
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr + 2u * (uint32_t)k[i]),
+                   "r"(r[2 * i]), "r"(r[2 * i + 1])
+                   : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+#endif
+  }
+  // zero the first n flows (2n columns, rounded up to 16)
+  __device__ __forceinline__ void zero(int n) const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+    for (int c = 0; c < 2 * n; c += 16)
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+          "%1, %1};" ::"r"(taddr + (uint32_t)c),
+          "r"(0u)
+          : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+#endif
+  }
+};
+
+}  // namespace mg

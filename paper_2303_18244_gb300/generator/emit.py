@@ -340,11 +340,19 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         if group:
             L.append(f"    pacc = pacc {'+' if psign[ai] > 0 else '-'} a;")
             if last_of[pid[ai]] == ai:
-                parts = []
-                for k, c in pats[pid[ai]]:
-                    parts.append(f"JAMP({k}) = JAMP({k}) {'+' if c > 0 else '-'} pacc;")
-                parts.append("pacc = cx<R>{R(0), R(0)};")
-                L.append("    " + " ".join(parts))
+                pat = pats[pid[ai]]
+                if mode == "chunked":
+                    kk = ", ".join(str(k) for k, _ in pat)
+                    sg = ", ".join("1" if c > 0 else "-1" for _, c in pat)
+                    L.append(f"    {{ constexpr int kk[{len(pat)}] = {{{kk}}}; constexpr int sg[{len(pat)}] = {{{sg}}};")
+                    L.append(f"      jamp.template update<{len(pat)}>(kk, sg, pacc); }}")
+                    L.append("    pacc = cx<R>{R(0), R(0)};")
+                else:
+                    parts = []
+                    for k, c in pat:
+                        parts.append(f"JAMP({k}) = JAMP({k}) {'+' if c > 0 else '-'} pacc;")
+                    parts.append("pacc = cx<R>{R(0), R(0)};")
+                    L.append("    " + " ".join(parts))
             L.append("  }")
             return
         parts = []
@@ -418,10 +426,9 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             emitted = {}
             emitted_k = set()
             imports = {c: slot_of[c] for c in cross if produced[c] < j and j in readers[c]}
-            L.append("template <typename R>")
+            L.append("template <typename R, typename J>")
             L.append(f"__device__ static __noinline__ void chunk{j}(const R* __restrict__ ev, const int es, "
-                     "const int hel, const double* __restrict__ kp, V4<R>* __restrict__ W, "
-                     "cx<R>* __restrict__ jamp, const int js) {")
+                     "const int hel, const double* __restrict__ kp, V4<R>* __restrict__ W, const J jamp) {")
             L.append("  const R g = R(kp[0]);")
             L.append("  const R mt = R(kp[1]);")
             for i in range(npar):
@@ -444,32 +451,36 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             chunk_funcs.append(L)
         L = main_L
         # the driver replaces the straight-line body begun above
-        while not L[-1].startswith("  for (int c = 0;"):
-            L.pop()
-        L.append(f"  V4<R> W[{nstore}];  // currents passed between chunks")
-        for j in range(len(chunks)):
-            L.append(f"  chunk{j}<R>(ev, es, hel, kp, W, jamp, js);")
-        L.append("#undef JAMP")
-        L.append("#undef EV")
-        L.append("}")
-        # chunk functions are emitted before amplitudes(): move them in front
         head = L.index("// one helicity: currents and amplitudes, diagram by diagram, into the colour flows")
-        body = L[head:]
         del L[head:]
         L.append("#define EV(k) ev[(k) * es]")
-        L.append("#define JAMP(k) jamp[(k) * js]")
         for f in chunk_funcs:
             L.extend(f)
-        L.append("#undef JAMP")
         L.append("#undef EV")
         L.append(f"static constexpr int NCHUNK = {len(chunks)};")
         L.append(f"static constexpr int NSTORE = {nstore};")
-        L.extend(body)
+        L.append("// one helicity: the chunks in order, the colour flows in the store J")
+        L.append("// (FlowsSmem: shared memory; FlowsTmem: tensor memory)")
+        L.append("template <typename R, typename J>")
+        L.append("__device__ static __forceinline__ void amplitudes_store(const R* __restrict__ ev, const int es, "
+                 "const int hel, const double* __restrict__ kp, const J jamp) {")
+        L.append(f"  V4<R> W[{nstore}];  // currents passed between chunks")
+        L.append("  jamp.zero(NCOL);")
+        for j in range(len(chunks)):
+            L.append(f"  chunk{j}<R, J>(ev, es, hel, kp, W, jamp);")
+        L.append("}")
+        L.append("template <typename R>")
+        L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")
+        L.append("                                           const double* __restrict__ kp, cx<R>* __restrict__ jamp,")
+        L.append("                                           const int js) {")
+        L.append("  amplitudes_store<R>(ev, es, hel, kp, FlowsSmem<R>{jamp, js});")
+        L.append("}")
         L.append("")
         L.extend(_colour_quadratic_looped(tag, ncol))
         L.append(f"}};  // struct {tag}")
         L.append("}  // namespace mg")
         src = "\n".join(L) + "\n"
+        src = src.replace('#include "mg_vertices.cuh"', '#include "mg_vertices.cuh"\n#include "mg_flowstore.cuh"', 1)
         return src.replace(f"struct {tag} {{", _knum_table(tag, K) + f"\nstruct {tag} {{", 1)
 
     if group:
