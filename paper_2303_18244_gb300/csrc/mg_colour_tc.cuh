@@ -473,12 +473,13 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-// First phase with the colour flows in tensor memory (MG_FLOWS_TMEM): 128
-// events per CTA, TMEM lane = event, two columns per flow; shared memory holds
-// only the momenta tile and the per-event slab, so that two CTAs (8 warps)
-// fit on an SM instead of two CTAs of 64 events.  Same output as flows_kernel.
+// First phase with the colour flows in tensor memory (default; MG_FLOWS_TMEM=0
+// selects flows_kernel): 128 events per CTA, TMEM lane = event, two columns
+// per flow; shared memory holds only the momenta tile and the per-event slab,
+// so that two CTAs (8 warps) fit on an SM instead of two CTAs of 64 events.
+// Same output as flows_kernel; gg -> t t~ g g g mixed 1.79e5 -> 2.87e5 MEs/s.
 #ifndef MG_FLOWS_TMEM
-#define MG_FLOWS_TMEM 0
+#define MG_FLOWS_TMEM 1
 #endif
 template <class P>
 struct LayoutFlowsTmem {
@@ -542,6 +543,132 @@ __global__ void __launch_bounds__(128)
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, LY::tmem_cols);
   }
+}
+
+// FP64 |M|^2 with the colour flows in tensor memory: 128 events per CTA,
+// four TMEM columns per flow (all 512 columns for 120 flows); shared memory
+// holds only the momenta tile and the FP64 slab, 4 warps per SM instead of 2.
+// The colour form reads the flows back from TMEM in blocks of four.
+template <class P>
+struct LayoutTmem64 {
+  static constexpr int NT = 128;
+  static constexpr size_t r128(size_t b) { return ((b + 127) / 128) * 128; }
+  static constexpr size_t bar_bytes = 128;  // TMA bar, TMEM address
+  static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
+  static constexpr size_t slab_bytes = size_t(NT) * slab_slots<P, double>() * sizeof(double);
+  static constexpr size_t stage_off = bar_bytes;
+  static constexpr size_t slab_off = stage_off + r128(stage_bytes);
+  static constexpr size_t base_bytes = slab_off + r128(slab_bytes);
+  static constexpr uint32_t tmem_cols = 512;
+};
+
+// four FP64 flows (16 columns) from TMEM
+__device__ __forceinline__ void tmem_flows4(uint32_t taddr, double re[4], double im[4]) {
+  float v[16];
+  tc::tmem_ld16(taddr, v);
+  tc::tmem_wait_ld();
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    re[q] = __hiloint2double(__float_as_int(v[4 * q + 1]), __float_as_int(v[4 * q]));
+    im[q] = __hiloint2double(__float_as_int(v[4 * q + 3]), __float_as_int(v[4 * q + 2]));
+  }
+}
+
+// sum_ij K_ij (Re J_i Re J_j + Im J_i Im J_j) from the FP64 flows in TMEM;
+// knum: K_ii on the diagonal, 2 K_ij for j > i
+template <class P>
+__device__ __forceinline__ double colour_tmem64(uint32_t taddr, const short* __restrict__ knum) {
+  static_assert(P::NCOL % 4 == 0, "blocks of four flows");
+  constexpr int NB = P::NCOL / 4;
+  double acc = 0.0;
+#pragma unroll 1
+  for (int ib = 0; ib < NB; ib++) {
+    double ri[4], ii[4], yr[4], yi[4];
+    tmem_flows4(taddr + 16u * ib, ri, ii);
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      yr[a] = 0.0;
+      yi[a] = 0.0;
+#pragma unroll
+      for (int b = a; b < 4; b++) {
+        const double k = (double)__ldg(knum + (4 * ib + a) * P::NCOL + 4 * ib + b);
+        yr[a] = ::fma(k, ri[b], yr[a]);
+        yi[a] = ::fma(k, ii[b], yi[a]);
+      }
+    }
+#pragma unroll 1
+    for (int jb = ib + 1; jb < NB; jb++) {
+      double rj[4], ij[4];
+      tmem_flows4(taddr + 16u * jb, rj, ij);
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+          const double k = (double)__ldg(knum + (4 * ib + a) * P::NCOL + 4 * jb + b);
+          yr[a] = ::fma(k, rj[b], yr[a]);
+          yi[a] = ::fma(k, ij[b], yi[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++) acc = ::fma(ri[a], yr[a], ::fma(ii[a], yi[a], acc));
+  }
+  return acc;
+}
+
+template <class P>
+__global__ void __launch_bounds__(128, 1)
+    sigma_tmem64_kernel(const double* __restrict__ mom, long long nevt, double* __restrict__ me,
+                        const int* __restrict__ hels, int nhel, KParams kp, unsigned* __restrict__ status) {
+  using LY = LayoutTmem64<P>;
+  constexpr int NT = 128;
+  static_assert(4 * P::NCOL <= (int)LY::tmem_cols, "flows fit in the allocated columns");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
+  double* stage = reinterpret_cast<double*>(smem + LY::stage_off);
+  double* slab = reinterpret_cast<double*>(smem + LY::slab_off);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int nvalid = load_and_prepare_at<P, double, NT>(tma_bar, stage, slab, mom, nevt, kp, status);
+  if (nvalid < 0) return;
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, LY::tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const FlowsTmem64 fl{tmem + ((uint32_t)(warp * 32) << 16)};
+  const short* knum = P::knum_dev();
+  double acc = 0.0;
+#pragma unroll 1
+  for (int ih = 0; ih < nhel; ih++) {
+    const int h = __ldg(hels + ih);
+    P::template amplitudes_store<double>(slab + tid, NT, h, kp.v, fl);
+    acc += colour_tmem64<P>(fl.taddr, knum);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, LY::tmem_cols);
+  }
+  if (tid < nvalid) {
+    constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+    me[(long long)blockIdx.x * NT + tid] = acc * norm;
+  }
+}
+
+template <class P>
+int launch_sigma_tmem64(const LaunchArgs& a) {
+  constexpr size_t smem = LayoutTmem64<P>::base_bytes;
+  static const cudaError_t attr = set_smem_attr(sigma_tmem64_kernel<P>, smem);
+  if (attr != cudaSuccess) return -4;
+  if (a.nevt <= 0) return 0;
+  sigma_tmem64_kernel<P><<<(unsigned)((a.nevt + 127) / 128), 128, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels,
+                                                                                     a.nhel, a.kp, a.status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 // The two phases over slices of the good helicities, every event in each

@@ -12,6 +12,7 @@
 //                 it keeps 120 complex flows per event off shared memory, so
 //                 that more events fit on an SM.  Warp-collective: every
 //                 thread of the warp must make the same calls.
+//   FlowsTmem64   the same for FP64 flows, four columns per flow.
 #pragma once
 
 #include "mg_vertices.cuh"
@@ -68,6 +69,56 @@ struct FlowsTmem {
 #ifdef __CUDA_ARCH__
     __syncwarp();
     for (int c = 0; c < 2 * n; c += 16)
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+          "%1, %1};" ::"r"(taddr + (uint32_t)c),
+          "r"(0u)
+          : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+#endif
+  }
+};
+
+// FP64 flows in tensor memory: four columns per flow (the two 32-bit halves
+// of Re, then of Im)
+struct FlowsTmem64 {
+  uint32_t taddr;
+  template <int N>
+  __device__ __forceinline__ void update(const int (&k)[N], const int (&sg)[N], cx<double> v) const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();  // the tcgen05 accesses below are warp-collective
+    uint32_t r[4 * N];
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(r[4 * i]), "=r"(r[4 * i + 1]), "=r"(r[4 * i + 2]), "=r"(r[4 * i + 3])
+                   : "r"(taddr + 4u * (uint32_t)k[i])
+                   : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const double re = __hiloint2double((int)r[4 * i + 1], (int)r[4 * i]);
+      const double im = __hiloint2double((int)r[4 * i + 3], (int)r[4 * i + 2]);
+      const double nre = sg[i] > 0 ? re + v.re : re - v.re;
+      const double nim = sg[i] > 0 ? im + v.im : im - v.im;
+      r[4 * i] = (uint32_t)__double2loint(nre);
+      r[4 * i + 1] = (uint32_t)__double2hiint(nre);
+      r[4 * i + 2] = (uint32_t)__double2loint(nim);
+      r[4 * i + 3] = (uint32_t)__double2hiint(nim);
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr + 4u * (uint32_t)k[i]),
+                   "r"(r[4 * i]), "r"(r[4 * i + 1]), "r"(r[4 * i + 2]), "r"(r[4 * i + 3])
+                   : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+#endif
+  }
+  // zero the first n flows (4n columns, rounded up to 16)
+  __device__ __forceinline__ void zero(int n) const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+    for (int c = 0; c < 4 * n; c += 16)
       asm volatile(
           "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
           "%1, %1};" ::"r"(taddr + (uint32_t)c),

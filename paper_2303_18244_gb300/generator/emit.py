@@ -732,6 +732,8 @@ def _colour_quadratic_looped(tag, ncol) -> list[str]:
     """sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j) as a loop over the device
     table (the straight-line form of a 120-flow process is too much code)."""
     L = []
+    L.append("// colour numerators in device memory: K_ii on the diagonal, 2 K_ij for j > i")
+    L.append(f"__device__ static const short* knum_dev() {{ return {tag}_KNUM; }}")
     L.append("// sum_ij KNUM_ij (Re J_i Re J_j + Im J_i Im J_j); |M|^2 colour sum = result / CDEN")
     L.append("template <typename R>")
     L.append("__device__ static __forceinline__ R colour_quadratic(const cx<R>* __restrict__ jamp, const int js) {")
@@ -1110,6 +1112,9 @@ THREADS = {
 TENSOR_CORE_COLOUR = {"ggttg", "ggttgg"}
 # tensor-core processes whose colour flows share the operand tiles' space
 TC_ALIAS = {"ggttgg"}
+# processes whose FP64 |M|^2 keeps the colour flows in tensor memory (120
+# complex FP64 flows per event do not fit in shared memory beside the slab)
+TMEM_FP64 = set(filter(None, os.environ.get("MG_TMEM_FP64", "ggttggg").split(",")))
 # processes whose mixed path writes the colour flows of every (helicity, event)
 # row to HBM and contracts them on the tensor cores in a second kernel
 # (120 flows: the operand tiles do not fit beside the per-event state)
@@ -1162,11 +1167,17 @@ int sigma_{tag}_float(const LaunchArgs& a) {{ return launch_sigma<{tag}, float, 
         return tag, src
     ncol = FIXED_NCOL.get(tag) or math.factorial(n)
     tck = ((ncol + 15) // 16) * 16 if tc else 0
+    if tag in TMEM_FP64:
+        inc64 = '#include "../mg_colour_tc.cuh"\n'
+        fp64 = f"launch_sigma_tmem64<{tag}>(a)"
+    else:
+        inc64 = ""
+        fp64 = f"launch_sigma<{tag}, double, {nt64}>(a)"
     src = f"""{head}#include "../mg_kernels.cuh"
-#include "{tag}.cuh"
+{inc64}#include "{tag}.cuh"
 
 namespace mg {{
-static int sigma_fp64(const LaunchArgs& a) {{ return launch_sigma<{tag}, double, {nt64}>(a); }}
+static int sigma_fp64(const LaunchArgs& a) {{ return {fp64}; }}
 static int helicities(const LaunchArgs& a) {{ return launch_helicities<{tag}, {nt64}>(a); }}
 static int select_fp64(const LaunchArgs& a) {{ return launch_select<{tag}, double, {nt64}>(a); }}
 static int paper(const LaunchArgs& a) {{ return launch_sigma_paper<{tag}, {nt64}>(a); }}
