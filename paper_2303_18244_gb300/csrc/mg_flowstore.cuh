@@ -34,6 +34,14 @@ struct FlowsSmem {
   __device__ __forceinline__ void zero(int n) const {
     for (int c = 0; c < n; c++) p[c * js] = cx<R>{R(0), R(0)};
   }
+  // add v to (or, odd entries, subtract it from) the flows of list[0..n)
+  __device__ __noinline__ void flush(const short* __restrict__ list, int n, cx<R> v) const {
+    for (int i = 0; i < n; i++) {
+      const int e = __ldg(list + i);
+      cx<R>& t = p[(e >> 1) * js];
+      t = (e & 1) ? t - v : t + v;
+    }
+  }
 };
 
 struct FlowsTmem {
@@ -61,6 +69,41 @@ struct FlowsTmem {
       asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr + 2u * (uint32_t)k[i]),
                    "r"(r[2 * i]), "r"(r[2 * i + 1])
                    : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+#endif
+  }
+  // add v to (odd entries: subtract it from) the flows of list[0..n), four
+  // flows per batch of loads and stores (n is the same for the whole warp)
+  __device__ __noinline__ void flush(const short* __restrict__ list, int n, cx<float> v) const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+    for (int i0 = 0; i0 < n; i0 += 4) {
+      const int m = n - i0 < 4 ? n - i0 : 4;
+      int e[4];
+      uint32_t r[8];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        e[j] = j < m ? __ldg(list + i0 + j) : 0;
+        if (j < m)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                       : "=r"(r[2 * j]), "=r"(r[2 * j + 1])
+                       : "r"(taddr + 2u * (uint32_t)(e[j] >> 1))
+                       : "memory");
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        if (j < m) {
+          const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
+          const bool minus = e[j] & 1;
+          r[2 * j] = __float_as_uint(minus ? re - v.re : re + v.re);
+          r[2 * j + 1] = __float_as_uint(minus ? im - v.im : im + v.im);
+          asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr + 2u * (uint32_t)(e[j] >> 1)),
+                       "r"(r[2 * j]), "r"(r[2 * j + 1])
+                       : "memory");
+        }
+      }
+    }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 #endif
   }
@@ -111,6 +154,42 @@ struct FlowsTmem64 {
       asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr + 4u * (uint32_t)k[i]),
                    "r"(r[4 * i]), "r"(r[4 * i + 1]), "r"(r[4 * i + 2]), "r"(r[4 * i + 3])
                    : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+#endif
+  }
+  __device__ __noinline__ void flush(const short* __restrict__ list, int n, cx<double> v) const {
+#ifdef __CUDA_ARCH__
+    __syncwarp();
+    for (int i0 = 0; i0 < n; i0 += 4) {
+      const int m = n - i0 < 4 ? n - i0 : 4;
+      int e[4];
+      uint32_t r[16];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        e[j] = j < m ? __ldg(list + i0 + j) : 0;
+        if (j < m)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(r[4 * j]), "=r"(r[4 * j + 1]), "=r"(r[4 * j + 2]), "=r"(r[4 * j + 3])
+                       : "r"(taddr + 4u * (uint32_t)(e[j] >> 1))
+                       : "memory");
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        if (j < m) {
+          const double re = __hiloint2double((int)r[4 * j + 1], (int)r[4 * j]);
+          const double im = __hiloint2double((int)r[4 * j + 3], (int)r[4 * j + 2]);
+          const bool minus = e[j] & 1;
+          const double nre = minus ? re - v.re : re + v.re;
+          const double nim = minus ? im - v.im : im + v.im;
+          asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                           taddr + 4u * (uint32_t)(e[j] >> 1)),
+                       "r"((uint32_t)__double2loint(nre)), "r"((uint32_t)__double2hiint(nre)),
+                       "r"((uint32_t)__double2loint(nim)), "r"((uint32_t)__double2hiint(nim))
+                       : "memory");
+        }
+      }
+    }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 #endif
   }

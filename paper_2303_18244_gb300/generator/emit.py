@@ -306,6 +306,12 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     # product V.J (gg -> t t~ g g: 74 pairs for 114 amplitudes, measured 6 %
     # faster in FP32, 11 % in FP64; MG_PAIR_V=0 turns it off)
     pair_v = os.environ.get("MG_PAIR_V", "1") == "1"
+    # chunked mode, MG_FLUSH_CALL=1: a colour pattern's flows are updated by one
+    # non-inlined call over its entry in a device table of (flow << 1 | minus)
+    # instead of inline code per pattern
+    flush_calls = os.environ.get("MG_FLUSH_CALL", "0") == "1"
+    flow_list: list = []
+    flow_list_off: dict = {}
     pair_uses: dict = {}
     for ai in amp_order:
         op = plan.amps[ai][0]
@@ -341,7 +347,14 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             L.append(f"    pacc = pacc {'+' if psign[ai] > 0 else '-'} a;")
             if last_of[pid[ai]] == ai:
                 pat = pats[pid[ai]]
-                if mode == "chunked":
+                if mode == "chunked" and flush_calls:
+                    # the pattern's flow list in the device table; one call
+                    off = flow_list_off.setdefault(pid[ai], len(flow_list))
+                    if off == len(flow_list):
+                        flow_list.extend((k << 1) | (1 if c < 0 else 0) for k, c in pat)
+                    L.append(f"    jamp.flush({tag}_FLOWLIST + {off}, {len(pat)}, pacc);")
+                    L.append("    pacc = cx<R>{R(0), R(0)};")
+                elif mode == "chunked":
                     kk = ", ".join(str(k) for k, _ in pat)
                     sg = ", ".join("1" if c > 0 else "-1" for _, c in pat)
                     L.append(f"    {{ constexpr int kk[{len(pat)}] = {{{kk}}}; constexpr int sg[{len(pat)}] = {{{sg}}};")
@@ -429,10 +442,10 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             L.append("template <typename R, typename J>")
             L.append(f"__device__ static __noinline__ void chunk{j}(const R* __restrict__ ev, const int es, "
                      "const int hel, const double* __restrict__ kp, V4<R>* __restrict__ W, const J jamp) {")
-            L.append("  const R g = R(kp[0]);")
-            L.append("  const R mt = R(kp[1]);")
+            L.append("  [[maybe_unused]] const R g = R(kp[0]);")
+            L.append("  [[maybe_unused]] const R mt = R(kp[1]);")
             for i in range(npar):
-                L.append(f"  const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
+                L.append(f"  [[maybe_unused]] const int l{i} = ((hel >> {npar - 1 - i}) & 1) ? 1 : -1;")
             L.append("  cx<R> pacc = {R(0), R(0)};")
             pair_names.clear()
             pair_uses.clear()
@@ -481,7 +494,11 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         L.append("}  // namespace mg")
         src = "\n".join(L) + "\n"
         src = src.replace('#include "mg_vertices.cuh"', '#include "mg_vertices.cuh"\n#include "mg_flowstore.cuh"', 1)
-        return src.replace(f"struct {tag} {{", _knum_table(tag, K) + f"\nstruct {tag} {{", 1)
+        tables = _knum_table(tag, K)
+        if flush_calls:
+            tables += (f"\nstatic __device__ const short {tag}_FLOWLIST[{max(1, len(flow_list))}] = {{"
+                       + ", ".join(str(v) for v in flow_list) + "};")
+        return src.replace(f"struct {tag} {{", tables + f"\nstruct {tag} {{", 1)
 
     if group:
         L.append("  cx<R> pacc = {R(0), R(0)};")
