@@ -110,8 +110,11 @@ int mg_good_helicities(mg_process* h, const double* momenta_dev, int64_t nevt, i
 
 /* ME per event on the device, stream-ordered and asynchronous:
  * me_out_dev[i] for momenta_dev[i], i < nevt.  nevt = 0 is a no-op.
+ * The mixed path of g g > t t~ g g g runs in two phases through a workspace
+ * of at most 1 GiB taken from the stream-ordered allocator (cudaMallocAsync)
+ * and released on the same stream (capturable in a CUDA graph).
  * Errors: MG_ERR_ARG (NULL handle/pointer, nevt < 0, misaligned momenta),
- * MG_ERR_CUDA (launch failure). */
+ * MG_ERR_CUDA (launch failure, or no memory for that workspace). */
 int mg_sigma(mg_process* h, const double* momenta_dev, int64_t nevt, double* me_out_dev, void* stream);
 
 /* Same computation from host buffers: copies momenta_host to a handle-owned
