@@ -115,7 +115,7 @@ def build(verbose: bool = True) -> str:
     tus.sort(key=weight)
     jobs = max(1, min(len(tus), os.cpu_count() or 1))
     with ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(_compile, tus))  # only this build's objects are linked
+        objs = list(ex.map(_compile, tus))  # only the objects of these sources are linked
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)

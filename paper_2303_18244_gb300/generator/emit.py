@@ -464,7 +464,7 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
             L.append("}")
             chunk_funcs.append(L)
         L = main_L
-        # the driver replaces the straight-line body begun above
+        # the chunk-calling amplitudes function replaces the straight-line body begun above
         head = L.index("// one helicity: currents and amplitudes, diagram by diagram, into the colour flows")
         del L[head:]
         L.append("#define EV(k) ev[(k) * es]")
