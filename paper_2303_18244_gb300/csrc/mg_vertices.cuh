@@ -35,6 +35,11 @@
 #ifndef MG_VERTEX_AMP
 #define MG_VERTEX_AMP MG_VERTEX
 #endif
+// MG_VERTEX_SMALL: the same for the shortest routines (vvvv_cur, vvvv_amp,
+// ffv_vcur), whose call overhead is a larger share of their work
+#ifndef MG_VERTEX_SMALL
+#define MG_VERTEX_SMALL MG_VERTEX
+#endif
 
 namespace mg {
 
@@ -478,7 +483,7 @@ __device__ MG_VERTEX Sp<R> ffv_col(const V4<R> J, const Sp<R> b, const M4<R> q, 
 
 // vector current coef * Fbar gamma^mu (cL PL + cR PR) F
 template <typename R>
-__device__ MG_VERTEX V4<R> ffv_vcur(const Sp<R> a, const Sp<R> b, cx<R> coef, R cL = R(1), R cR = R(1)) {
+__device__ MG_VERTEX_SMALL V4<R> ffv_vcur(const Sp<R> a, const Sp<R> b, cx<R> coef, R cL = R(1), R cR = R(1)) {
   // upper: (a0,a1) sigma^mu (b2,b3) [right-handed F], lower: (a2,a3) sigmabar^mu (b0,b1)
   const cx<R> u02 = a.c[0] * b.c[2], u13 = a.c[1] * b.c[3], u03 = a.c[0] * b.c[3], u12 = a.c[1] * b.c[2];
   const cx<R> l20 = a.c[2] * b.c[0], l31 = a.c[3] * b.c[1], l21 = a.c[2] * b.c[1], l30 = a.c[3] * b.c[0];
@@ -530,7 +535,7 @@ __device__ MG_VERTEX_AMP cx<R> vvv_amp(const M4<R> kx, const V4<R> Jx, const M4<
 // four-gluon Lorentz structures for the three colour branches
 //   br 0: (X.Z) Y - (Y.Z) X     br 1: (X.Y) Z - (Y.Z) X     br 2: (X.Y) Z - (X.Z) Y
 template <int BR, typename R>
-__device__ MG_VERTEX V4<R> vvvv_cur(const V4<R> X, const V4<R> Y, const V4<R> Z, R c) {
+__device__ MG_VERTEX_SMALL V4<R> vvvv_cur(const V4<R> X, const V4<R> Y, const V4<R> Z, R c) {
   V4<R> o;
   if (BR == 0) {
     const cx<R> xz = dot(X, Z), yz = dot(Y, Z);
@@ -545,7 +550,7 @@ __device__ MG_VERTEX V4<R> vvvv_cur(const V4<R> X, const V4<R> Y, const V4<R> Z,
   return o;
 }
 template <int BR, typename R>
-__device__ MG_VERTEX_AMP cx<R> vvvv_amp(const V4<R> X, const V4<R> Y, const V4<R> Z, const V4<R> G, R c) {
+__device__ MG_VERTEX_SMALL cx<R> vvvv_amp(const V4<R> X, const V4<R> Y, const V4<R> Z, const V4<R> G, R c) {
   cx<R> t;
   if (BR == 0) t = dot(X, Z) * dot(Y, G) - dot(Y, Z) * dot(X, G);
   else if (BR == 1) t = dot(X, Y) * dot(Z, G) - dot(Y, Z) * dot(X, G);
