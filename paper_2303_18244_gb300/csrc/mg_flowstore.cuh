@@ -17,6 +17,13 @@
 
 #include "mg_vertices.cuh"
 
+// MG_CHUNK_SYNC=1: the tensor-memory stores put a block barrier after each
+// chunk of the helicity program, so that the CTA's warps run the same chunk's
+// code together (every thread of the CTA runs the program)
+#ifndef MG_CHUNK_SYNC
+#define MG_CHUNK_SYNC 0
+#endif
+
 namespace mg {
 
 template <typename R>
@@ -34,6 +41,7 @@ struct FlowsSmem {
   __device__ __forceinline__ void zero(int n) const {
     for (int c = 0; c < n; c++) p[c * js] = cx<R>{R(0), R(0)};
   }
+  __device__ __forceinline__ void chunk_done() const {}
   // add v to (or, odd entries, subtract it from) the flows of list[0..n)
   __device__ __noinline__ void flush(const short* __restrict__ list, int n, cx<R> v) const {
     for (int i = 0; i < n; i++) {
@@ -46,6 +54,9 @@ struct FlowsSmem {
 
 struct FlowsTmem {
   uint32_t taddr;  // lane (bits 16-31) and first column of the thread's flows
+  __device__ __forceinline__ void chunk_done() const {
+    if constexpr (MG_CHUNK_SYNC != 0) __syncthreads();
+  }
   template <int N>
   __device__ __forceinline__ void update(const int (&k)[N], const int (&sg)[N], cx<float> v) const {
 #ifdef __CUDA_ARCH__
@@ -126,6 +137,9 @@ struct FlowsTmem {
 // of Re, then of Im)
 struct FlowsTmem64 {
   uint32_t taddr;
+  __device__ __forceinline__ void chunk_done() const {
+    if constexpr (MG_CHUNK_SYNC != 0) __syncthreads();
+  }
   template <int N>
   __device__ __forceinline__ void update(const int (&k)[N], const int (&sg)[N], cx<double> v) const {
 #ifdef __CUDA_ARCH__

@@ -482,6 +482,8 @@ def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
         L.append("  jamp.zero(NCOL);")
         for j in range(len(chunks)):
             L.append(f"  chunk{j}<R, J>(ev, es, hel, kp, W, jamp);")
+            if j + 1 < len(chunks):
+                L.append("  jamp.chunk_done();")
         L.append("}")
         L.append("template <typename R>")
         L.append("__device__ static __forceinline__ void amplitudes(const R* __restrict__ ev, const int es, const int hel,")

@@ -318,3 +318,66 @@ def test_fp64_ill_conditioned_event_against_extended_oracle():
     ext = O.me(proc, p, extended=True)
     assert _rel(got, ext).max() <= 1e-12
     assert _rel(O.me(proc, p), ext).max() > 1e-10  # the FP64 oracle itself does not
+
+
+# (process, precision, batch size): batch * npar * 4 > 2^31 momentum elements
+LARGE = [
+    ("g g > t t~", mg.MG_FP64, (1 << 27) + (1 << 20) + 77),
+    ("g g > t t~", mg.MG_MIXED, (1 << 27) + (1 << 20) + 77),
+    ("g g > t t~ g g", mg.MG_MIXED, 89_478_485 + 65536 + 45),
+]
+
+
+@pytest.mark.parametrize("proc,precision,nevt", LARGE, ids=["ggtt-fp64", "ggtt-mixed", "ggttgg-mixed"])
+def test_element_offsets_beyond_32_bits(proc, precision, nevt):
+    """Maximum sizes: more than 2^31 momentum elements (17 GB on the device),
+    so every offset past 2^31 must be 64-bit.  The batch repeats a block of
+    4099 (prime) events: an offset that wrapped at 2^31 elements, or a result
+    written to the wrong slot, would pair an event with another event's
+    value.  Every copy of an event must give the block's value (a property of
+    the whole 1e8-event output), and events on both sides of the
+    2^31-element boundary, in the ragged tail and at the start are compared
+    with the oracle."""
+    rs, seed, _, _ = WORKLOADS[proc]
+    h = mg.Process(proc, precision=precision)
+    npar = h.info.npar
+    need = nevt * (npar * 4 * 8 + 8 + 1) + (1 << 30)
+    free, _ = torch.cuda.mem_get_info()
+    if free < need:
+        pytest.skip(f"needs {need / 1e9:.1f} GB of free device memory, {free / 1e9:.1f} GB free")
+    B = 4099
+    block = process_momenta(proc, rs, B, seed + 2000)
+    blk = _dev(block)
+    mom = torch.empty((nevt, npar, 4), dtype=torch.float64, device="cuda")
+    reps = nevt // B
+    mom[: reps * B].view(reps, B, npar, 4).copy_(blk.unsqueeze(0).expand(reps, B, npar, 4))
+    mom[reps * B:].copy_(blk[: nevt - reps * B])
+    out = torch.full((nevt,), float("nan"), dtype=torch.float64, device="cuda")
+    mg.good_helicities(h, _dev(process_momenta(proc, rs, 1024, seed + 1000)))
+    mg.sigma(h, mom, out)
+    torch.cuda.synchronize()
+    assert mg.process_status(h) == 0
+    del mom
+    head = out[:B]
+    assert bool(torch.isfinite(out).all()) and bool((out > 0).all())
+    dev = (out[: reps * B].view(reps, B) - head).abs() / head
+    tail = (out[reps * B:] - head[: nevt - reps * B]).abs() / head[: nevt - reps * B]
+    worst = max(float(dev.max()), float(tail.max()) if tail.numel() else 0.0)
+    print(f"{proc} nevt {nevt}: largest deviation between copies of an event {worst:.2e}")
+    # FP64: one thread per event, the same instructions wherever the event
+    # sits; mixed: the same, bar any dependence of the tensor-core rows on
+    # their TMEM lane
+    assert worst <= (0.0 if precision == mg.MG_FP64 else 1e-6)
+    cross = -(-(1 << 31) // (npar * 4))  # first event at element offset >= 2^31
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([
+        [0, 1, 127, 128, cross - 129, cross - 1, cross, cross + 1, cross + 127, cross + 128,
+         nevt - 130, nevt - 2, nevt - 1], rng.integers(0, nevt, 16)]))
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    p = block[idx % B]
+    ref = O.me(proc, p)
+    if precision == mg.MG_FP64:
+        _assert_fp64(proc, p, got, ref)
+    else:
+        r = _rel(got, ref)
+        assert np.median(r) <= 1e-5 and r.max() <= 1e-2
