@@ -136,6 +136,85 @@ struct LayoutTC {
   static constexpr uint32_t tmem_cols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
 };
 
+// The per-helicity colour form of a CTA of 128 events, shared by the fused
+// kernels.  (1) Each event's thread writes its flows, scaled by a power of two
+// s = 2^-ex that puts max |J| in [1, 2), as FP16 hi + lo into the four operand
+// tiles (re_hi, re_lo, im_hi, im_lo; row = event); returns s.
+template <class P, int K>
+__device__ __forceinline__ float colour_operands(unsigned char* atile, size_t a_tile, int row,
+                                                 const float (&fr)[P::NCOL], const float (&fi)[P::NCOL]) {
+  float mx = 0.f;
+#pragma unroll
+  for (int k = 0; k < P::NCOL; k++) mx = fmaxf(mx, fmaxf(fabsf(fr[k]), fabsf(fi[k])));
+  const int ex = mx > 0.f ? ((int)((__float_as_uint(mx) >> 23) & 0xff) - 127) : 0;
+  const float s = __uint_as_float((uint32_t)(127 - ex) << 23);  // 2^-ex
+#pragma unroll
+  for (int j = 0; j < K / 8; j++) {
+    __align__(16) __half hr[8], lr[8], hi_[8], li[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int k = 8 * j + q;
+      const float xr = k < P::NCOL ? s * fr[k < P::NCOL ? k : 0] : 0.f;
+      const float xi = k < P::NCOL ? s * fi[k < P::NCOL ? k : 0] : 0.f;
+      hr[q] = __float2half_rn(xr);
+      lr[q] = __float2half_rn(xr - __half2float(hr[q]));
+      hi_[q] = __float2half_rn(xi);
+      li[q] = __float2half_rn(xi - __half2float(hi_[q]));
+    }
+    const uint32_t off = tc::tile_off(row, 8 * j, K);
+    *reinterpret_cast<uint4*>(atile + 0 * a_tile + off) = *reinterpret_cast<const uint4*>(hr);
+    *reinterpret_cast<uint4*>(atile + 1 * a_tile + off) = *reinterpret_cast<const uint4*>(lr);
+    *reinterpret_cast<uint4*>(atile + 2 * a_tile + off) = *reinterpret_cast<const uint4*>(hi_);
+    *reinterpret_cast<uint4*>(atile + 3 * a_tile + off) = *reinterpret_cast<const uint4*>(li);
+  }
+  return s;
+}
+
+// (2) One elected thread: D_re = (A_re_hi + A_re_lo) . KNUM into TMEM columns
+// [0, N), D_im likewise into [N, 2N); completion arrives on mma_bar.
+template <int K, int N>
+__device__ __forceinline__ void colour_mma(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, size_t a_tile,
+                                           uint64_t* mma_bar) {
+  constexpr uint32_t idesc = tc::idesc_f16(128, N);
+  constexpr uint32_t SBO = (K / 8) * 128;
+  tc::fence_after_sync();
+  for (int part = 0; part < 2; part++) {  // 0: Re -> columns [0, N), 1: Im -> [N, 2N)
+    const uint32_t d = tmem + part * N;
+    for (int kk = 0; kk < K / 16; kk++) {
+      const uint64_t bd = tc::smem_desc(b_addr + kk * 2 * tc::LBO, tc::LBO, SBO);
+      const uint32_t hi_base = a_addr + (2 * part) * (uint32_t)a_tile + kk * 2 * tc::LBO;
+      const uint32_t lo_base = a_addr + (2 * part + 1) * (uint32_t)a_tile + kk * 2 * tc::LBO;
+      tc::mma_f16(d, tc::smem_desc(hi_base, tc::LBO, SBO), bd, idesc, kk > 0 ? 1u : 0u);
+      tc::mma_f16(d, tc::smem_desc(lo_base, tc::LBO, SBO), bd, idesc, 1u);
+    }
+  }
+  tc::mma_commit(mma_bar);
+}
+
+// (3) Warp-collective: the event's row of D read from its TMEM lane and
+// contracted with its flows, sum_k Re J_k D_re,k + Im J_k D_im,k (still
+// scaled by s).
+template <class P, int N>
+__device__ __forceinline__ float colour_readback(uint32_t lane_base, const float (&fr)[P::NCOL],
+                                                 const float (&fi)[P::NCOL]) {
+  float dsum = 0.f;
+#pragma unroll
+  for (int c = 0; c < N; c += 16) {
+    float dr[16], di[16];
+    tc::tmem_ld16(lane_base + c, dr);
+    tc::tmem_ld16(lane_base + N + c, di);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+      if (c + q < P::NCOL) {
+        dsum = fmaf(fr[c + q < P::NCOL ? c + q : 0], dr[q], dsum);
+        dsum = fmaf(fi[c + q < P::NCOL ? c + q : 0], di[q], dsum);
+      }
+    }
+  }
+  return dsum;
+}
+
 // CTAs per SM the register allocation is sized for (launch bounds).  At 2 the
 // straight-line gg -> t t~ g g code keeps 255 registers; 3 caps them at 168 and
 // its spills halve the throughput (measured).
@@ -185,11 +264,8 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-  constexpr uint32_t idesc = tc::idesc_f16(128, N);
   const uint32_t a_addr = smem_u32(atile);
   const uint32_t b_addr = smem_u32(btile);
-  constexpr uint32_t SBO_A = (K / 8) * 128;
-  constexpr uint32_t SBO_B = (K / 8) * 128;
 
   double acc = 0.0;
   uint32_t phase = 0;
@@ -207,46 +283,10 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
     }
     if constexpr (LY::alias) __syncthreads();
     // per-event power-of-two scale, FP16 hi/lo split into the operand tiles
-    float mx = 0.f;
-#pragma unroll
-    for (int k = 0; k < P::NCOL; k++) mx = fmaxf(mx, fmaxf(fabsf(fr[k]), fabsf(fi[k])));
-    const int ex = mx > 0.f ? ((int)((__float_as_uint(mx) >> 23) & 0xff) - 127) : 0;
-    const float s = __uint_as_float((uint32_t)(127 - ex) << 23);  // 2^-ex
-#pragma unroll
-    for (int j = 0; j < K / 8; j++) {
-      __align__(16) __half hr[8], lr[8], hi_[8], li[8];
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const int k = 8 * j + q;
-        const float xr = k < P::NCOL ? s * fr[k < P::NCOL ? k : 0] : 0.f;
-        const float xi = k < P::NCOL ? s * fi[k < P::NCOL ? k : 0] : 0.f;
-        hr[q] = __float2half_rn(xr);
-        lr[q] = __float2half_rn(xr - __half2float(hr[q]));
-        hi_[q] = __float2half_rn(xi);
-        li[q] = __float2half_rn(xi - __half2float(hi_[q]));
-      }
-      const uint32_t off = tc::tile_off(tid, 8 * j, K);
-      *reinterpret_cast<uint4*>(atile + 0 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(hr);
-      *reinterpret_cast<uint4*>(atile + 1 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(lr);
-      *reinterpret_cast<uint4*>(atile + 2 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(hi_);
-      *reinterpret_cast<uint4*>(atile + 3 * LY::a_tile + off) = *reinterpret_cast<const uint4*>(li);
-    }
+    const float s = colour_operands<P, K>(atile, LY::a_tile, tid, fr, fi);
     fence_proxy_async_smem();  // generic-proxy tile writes -> visible to the tensor core
     __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int part = 0; part < 2; part++) {  // 0: Re -> columns [0, N), 1: Im -> [N, 2N)
-        const uint32_t d = tmem + part * N;
-        for (int kk = 0; kk < K / 16; kk++) {
-          const uint64_t bd = tc::smem_desc(b_addr + kk * 2 * tc::LBO, tc::LBO, SBO_B);
-          const uint32_t hi_base = a_addr + (2 * part) * (uint32_t)LY::a_tile + kk * 2 * tc::LBO;
-          const uint32_t lo_base = a_addr + (2 * part + 1) * (uint32_t)LY::a_tile + kk * 2 * tc::LBO;
-          tc::mma_f16(d, tc::smem_desc(hi_base, tc::LBO, SBO_A), bd, idesc, kk > 0 ? 1u : 0u);
-          tc::mma_f16(d, tc::smem_desc(lo_base, tc::LBO, SBO_A), bd, idesc, 1u);
-        }
-      }
-      tc::mma_commit(mma_bar);
-    }
+    if (tid == 0) colour_mma<K, N>(tmem, a_addr, b_addr, LY::a_tile, mma_bar);
     // the outcome of the bounded wait is made uniform across the CTA, so that
     // no thread can skip the warp-collective TMEM loads or a barrier alone
     if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, WAIT_POLLS) ? 1 : 0)) {
@@ -256,21 +296,7 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
     }
     phase ^= 1u;
     tc::fence_after_sync();
-    float dsum = 0.f;
-#pragma unroll
-    for (int c = 0; c < N; c += 16) {
-      float dr[16], di[16];
-      tc::tmem_ld16(lane_base + c, dr);
-      tc::tmem_ld16(lane_base + N + c, di);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int q = 0; q < 16; q++) {
-        if (c + q < P::NCOL) {
-          dsum = fmaf(fr[c + q < P::NCOL ? c + q : 0], dr[q], dsum);
-          dsum = fmaf(fi[c + q < P::NCOL ? c + q : 0], di[q], dsum);
-        }
-      }
-    }
+    const float dsum = colour_readback<P, N>(lane_base, fr, fi);
     acc += (double)(dsum / s);
     tc::fence_before_sync();
     __syncthreads();  // tiles and accumulators are reused by the next helicity
@@ -287,6 +313,134 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
     tc::tmem_dealloc(tmem, LY::tmem_cols);
   }
   if (ok && tid < nvalid) {
+    constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
+    me[(long long)blockIdx.x * NT + tid] = acc * norm;
+  }
+}
+
+// Split program: two threads per event.  Warps 0-3 run the first half of the
+// scheduled amplitudes (with the currents they need) for the CTA's 128 events,
+// warps 4-7 the second half for the same events, each into its own colour
+// flows; threads 0-127 add the two flow sets and run the colour form as above.
+// Each thread keeps about half the live values of the whole program, so the
+// register cap of two 256-thread CTAs per SM (128) holds 16 warps per SM
+// where the whole program (255 registers) holds 8.  Shared memory: the
+// momenta tile, both flow sets and the operand tiles take turns in one region.
+template <class P>
+struct LayoutSplit {
+  static constexpr int NT = 128;  // events per CTA; 2 NT threads
+  static constexpr int K = tc::pad16(P::NCOL);
+  static constexpr int N = tc::pad16(P::NCOL);
+  static constexpr size_t r128(size_t b) { return ((b + 127) / 128) * 128; }
+  static constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+  static constexpr size_t a_tile = size_t(NT) * K * 2;  // FP16 [NT][K]
+  static constexpr size_t b_tile = size_t(N) * K * 2;   // FP16 [N][K]
+  static constexpr size_t bar_bytes = 128;
+  static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
+  static constexpr size_t flows_bytes = r128(size_t(NT) * P::NCOL * sizeof(cx<float>));  // one flow set
+  static constexpr size_t slab_bytes = size_t(NT) * slab_slots<P, float>() * sizeof(float);
+  static constexpr size_t region_bytes = cmax(cmax(stage_bytes, 4 * a_tile), 2 * flows_bytes);
+  static constexpr size_t region_off = bar_bytes;
+  static constexpr size_t b_off = region_off + r128(region_bytes);
+  static constexpr size_t slab_off = b_off + r128(b_tile);
+  static constexpr size_t base_bytes = slab_off + r128(slab_bytes);
+  static constexpr uint32_t tmem_cols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
+};
+
+// CTAs of 256 threads per SM the split program's registers are sized for
+#ifndef MG_SPLIT_MINB
+#define MG_SPLIT_MINB 2
+#endif
+
+template <class P>
+__global__ void __launch_bounds__(256, MG_SPLIT_MINB) sigma_tc_split_kernel(
+    const double* __restrict__ mom, long long nevt, double* __restrict__ me, const int* __restrict__ hels, int nhel,
+    KParams kp, const uint4* __restrict__ ctile, unsigned* __restrict__ status) {
+  using LY = LayoutSplit<P>;
+  constexpr int NT = LY::NT, K = LY::K, N = LY::N;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* mma_bar = reinterpret_cast<uint64_t*>(smem + 16);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 32);
+  unsigned char* region = smem + LY::region_off;
+  float* slab = reinterpret_cast<float*>(smem + LY::slab_off);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const bool second = tid >= NT;  // runs the second half of the program
+  const int e = second ? tid - NT : tid;  // the thread's event in the CTA
+  cx<float>* flows0 = reinterpret_cast<cx<float>*>(region) + e;
+  cx<float>* flows1 = reinterpret_cast<cx<float>*>(region + LY::flows_bytes) + e;
+
+  const int nvalid =
+      load_and_prepare_at<P, float, NT>(tma_bar, reinterpret_cast<double*>(region), slab, mom, nevt, kp, status);
+  if (nvalid < 0) return;  // (load_and_prepare_at ends with a block barrier: the tile space is free)
+
+  unsigned char* atile = region;  // 4 tiles: re_hi, re_lo, im_hi, im_lo
+  unsigned char* btile = smem + LY::b_off;
+  for (int i = tid; i < (int)(LY::b_tile / 16); i += 2 * NT)
+    reinterpret_cast<uint4*>(btile)[i] = __ldg(ctile + i);
+  if (tid == 0) {
+    mbar_init(mma_bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_slot, LY::tmem_cols);
+    tc::tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t a_addr = smem_u32(atile);
+  const uint32_t b_addr = smem_u32(btile);
+
+  double acc = 0.0;
+  uint32_t phase = 0;
+  bool ok = true;
+#pragma unroll 1
+  for (int ih = 0; ih < nhel && ok; ih++) {
+    const int h = __ldg(hels + ih);
+    if (second)
+      P::template amplitudes_half1<float>(slab + e, NT, h, kp.v, flows1, NT);
+    else
+      P::template amplitudes_half0<float>(slab + e, NT, h, kp.v, flows0, NT);
+    __syncthreads();  // both flow sets are complete
+    float fr[P::NCOL], fi[P::NCOL];
+    if (!second) {
+#pragma unroll
+      for (int k = 0; k < P::NCOL; k++) {
+        fr[k] = flows0[k * NT].re + flows1[k * NT].re;
+        fi[k] = flows0[k * NT].im + flows1[k * NT].im;
+      }
+    }
+    __syncthreads();  // the flows' space takes the operand tiles
+    float s = 1.f;
+    if (!second) s = colour_operands<P, K>(atile, LY::a_tile, e, fr, fi);
+    fence_proxy_async_smem();  // generic-proxy tile writes -> visible to the tensor core
+    __syncthreads();
+    if (tid == 0) colour_mma<K, N>(tmem, a_addr, b_addr, LY::a_tile, mma_bar);
+    // bounded wait, outcome uniform across the CTA (see sigma_tc_kernel)
+    if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, WAIT_POLLS) ? 1 : 0)) {
+      if (tid == 0) atomicOr(status, ST_MMA_TIMEOUT);
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!second) acc += (double)(colour_readback<P, N>(lane_base, fr, fi) / s);  // warps 0-3: whole warps
+    tc::fence_before_sync();
+    __syncthreads();  // tiles and accumulators are reused by the next helicity
+  }
+  if (!ok) mbar_wait_bounded(mma_bar, phase, WAIT_POLLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, LY::tmem_cols);
+  }
+  if (ok && tid < nvalid) {  // nvalid <= NT: first-half threads only
     constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
     me[(long long)blockIdx.x * NT + tid] = acc * norm;
   }
@@ -712,6 +866,18 @@ int launch_sigma_rows(const LaunchArgs& a) {
   const cudaError_t e1 = cudaGetLastError();
   const cudaError_t e2 = cudaFreeAsync(J, a.stream);
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -4;
+}
+
+template <class P>
+int launch_sigma_tc_split(const LaunchArgs& a) {
+  constexpr size_t smem = LayoutSplit<P>::base_bytes;
+  static const cudaError_t attr = set_smem_attr(sigma_tc_split_kernel<P>, smem);
+  if (attr != cudaSuccess) return -4;
+  if (a.nevt <= 0) return 0;
+  const long long grid = (a.nevt + 127) / 128;
+  sigma_tc_split_kernel<P><<<(unsigned)grid, 256, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels, a.nhel, a.kp,
+                                                                      static_cast<const uint4*>(a.ctile), a.status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 template <class P>
