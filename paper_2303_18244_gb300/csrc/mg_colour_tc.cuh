@@ -318,134 +318,6 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
   }
 }
 
-// Split program: two threads per event.  Warps 0-3 run the first half of the
-// scheduled amplitudes (with the currents they need) for the CTA's 128 events,
-// warps 4-7 the second half for the same events, each into its own colour
-// flows; threads 0-127 add the two flow sets and run the colour form as above.
-// Each thread keeps about half the live values of the whole program, so the
-// register cap of two 256-thread CTAs per SM (128) holds 16 warps per SM
-// where the whole program (255 registers) holds 8.  Shared memory: the
-// momenta tile, both flow sets and the operand tiles take turns in one region.
-template <class P>
-struct LayoutSplit {
-  static constexpr int NT = 128;  // events per CTA; 2 NT threads
-  static constexpr int K = tc::pad16(P::NCOL);
-  static constexpr int N = tc::pad16(P::NCOL);
-  static constexpr size_t r128(size_t b) { return ((b + 127) / 128) * 128; }
-  static constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-  static constexpr size_t a_tile = size_t(NT) * K * 2;  // FP16 [NT][K]
-  static constexpr size_t b_tile = size_t(N) * K * 2;   // FP16 [N][K]
-  static constexpr size_t bar_bytes = 128;
-  static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
-  static constexpr size_t flows_bytes = r128(size_t(NT) * P::NCOL * sizeof(cx<float>));  // one flow set
-  static constexpr size_t slab_bytes = size_t(NT) * slab_slots<P, float>() * sizeof(float);
-  static constexpr size_t region_bytes = cmax(cmax(stage_bytes, 4 * a_tile), 2 * flows_bytes);
-  static constexpr size_t region_off = bar_bytes;
-  static constexpr size_t b_off = region_off + r128(region_bytes);
-  static constexpr size_t slab_off = b_off + r128(b_tile);
-  static constexpr size_t base_bytes = slab_off + r128(slab_bytes);
-  static constexpr uint32_t tmem_cols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
-};
-
-// CTAs of 256 threads per SM the split program's registers are sized for
-#ifndef MG_SPLIT_MINB
-#define MG_SPLIT_MINB 2
-#endif
-
-template <class P>
-__global__ void __launch_bounds__(256, MG_SPLIT_MINB) sigma_tc_split_kernel(
-    const double* __restrict__ mom, long long nevt, double* __restrict__ me, const int* __restrict__ hels, int nhel,
-    KParams kp, const uint4* __restrict__ ctile, unsigned* __restrict__ status) {
-  using LY = LayoutSplit<P>;
-  constexpr int NT = LY::NT, K = LY::K, N = LY::N;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* mma_bar = reinterpret_cast<uint64_t*>(smem + 16);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 32);
-  unsigned char* region = smem + LY::region_off;
-  float* slab = reinterpret_cast<float*>(smem + LY::slab_off);
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const bool second = tid >= NT;  // runs the second half of the program
-  const int e = second ? tid - NT : tid;  // the thread's event in the CTA
-  cx<float>* flows0 = reinterpret_cast<cx<float>*>(region) + e;
-  cx<float>* flows1 = reinterpret_cast<cx<float>*>(region + LY::flows_bytes) + e;
-
-  const int nvalid =
-      load_and_prepare_at<P, float, NT>(tma_bar, reinterpret_cast<double*>(region), slab, mom, nevt, kp, status);
-  if (nvalid < 0) return;  // (load_and_prepare_at ends with a block barrier: the tile space is free)
-
-  unsigned char* atile = region;  // 4 tiles: re_hi, re_lo, im_hi, im_lo
-  unsigned char* btile = smem + LY::b_off;
-  for (int i = tid; i < (int)(LY::b_tile / 16); i += 2 * NT)
-    reinterpret_cast<uint4*>(btile)[i] = __ldg(ctile + i);
-  if (tid == 0) {
-    mbar_init(mma_bar, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    tc::tmem_alloc(tmem_slot, LY::tmem_cols);
-    tc::tmem_relinquish();
-  }
-  fence_proxy_async_smem();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  const uint32_t a_addr = smem_u32(atile);
-  const uint32_t b_addr = smem_u32(btile);
-
-  double acc = 0.0;
-  uint32_t phase = 0;
-  bool ok = true;
-#pragma unroll 1
-  for (int ih = 0; ih < nhel && ok; ih++) {
-    const int h = __ldg(hels + ih);
-    if (second)
-      P::template amplitudes_half1<float>(slab + e, NT, h, kp.v, flows1, NT);
-    else
-      P::template amplitudes_half0<float>(slab + e, NT, h, kp.v, flows0, NT);
-    __syncthreads();  // both flow sets are complete
-    float fr[P::NCOL], fi[P::NCOL];
-    if (!second) {
-#pragma unroll
-      for (int k = 0; k < P::NCOL; k++) {
-        fr[k] = flows0[k * NT].re + flows1[k * NT].re;
-        fi[k] = flows0[k * NT].im + flows1[k * NT].im;
-      }
-    }
-    __syncthreads();  // the flows' space takes the operand tiles
-    float s = 1.f;
-    if (!second) s = colour_operands<P, K>(atile, LY::a_tile, e, fr, fi);
-    fence_proxy_async_smem();  // generic-proxy tile writes -> visible to the tensor core
-    __syncthreads();
-    if (tid == 0) colour_mma<K, N>(tmem, a_addr, b_addr, LY::a_tile, mma_bar);
-    // bounded wait, outcome uniform across the CTA (see sigma_tc_kernel)
-    if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, WAIT_POLLS) ? 1 : 0)) {
-      if (tid == 0) atomicOr(status, ST_MMA_TIMEOUT);
-      ok = false;
-      break;
-    }
-    phase ^= 1u;
-    tc::fence_after_sync();
-    if (!second) acc += (double)(colour_readback<P, N>(lane_base, fr, fi) / s);  // warps 0-3: whole warps
-    tc::fence_before_sync();
-    __syncthreads();  // tiles and accumulators are reused by the next helicity
-  }
-  if (!ok) mbar_wait_bounded(mma_bar, phase, WAIT_POLLS);
-  tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) {
-    tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, LY::tmem_cols);
-  }
-  if (ok && tid < nvalid) {  // nvalid <= NT: first-half threads only
-    constexpr double norm = 1.0 / (P::IDEN * P::CDEN);
-    me[(long long)blockIdx.x * NT + tid] = acc * norm;
-  }
-}
-
 // FP16 bit pattern of an integer, or -1 if it is not exactly representable.
 inline int fp16_bits_of_int(int v) {
   if (v == 0) return 0;
@@ -866,18 +738,6 @@ int launch_sigma_rows(const LaunchArgs& a) {
   const cudaError_t e1 = cudaGetLastError();
   const cudaError_t e2 = cudaFreeAsync(J, a.stream);
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : -4;
-}
-
-template <class P>
-int launch_sigma_tc_split(const LaunchArgs& a) {
-  constexpr size_t smem = LayoutSplit<P>::base_bytes;
-  static const cudaError_t attr = set_smem_attr(sigma_tc_split_kernel<P>, smem);
-  if (attr != cudaSuccess) return -4;
-  if (a.nevt <= 0) return 0;
-  const long long grid = (a.nevt + 127) / 128;
-  sigma_tc_split_kernel<P><<<(unsigned)grid, 256, smem, a.stream>>>(a.mom, a.nevt, a.out, a.hels, a.nhel, a.kp,
-                                                                      static_cast<const uint4*>(a.ctile), a.status);
-  return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 template <class P>

@@ -135,8 +135,7 @@ __device__ __forceinline__ int load_and_prepare_at(uint64_t* bar, double* stage,
     return -1;
   }
   const int le = tid < nvalid ? tid : nvalid - 1;  // ragged tail: repeat a valid event
-  if (tid < NT)  // (CTAs of the split program have two threads per event)
-    P::template prepare<R, D>(stage + le * P::NPAR * 4, kp.v, slab + tid, NT);
+  P::template prepare<R, D>(stage + le * P::NPAR * 4, kp.v, slab + tid, NT);
   __syncthreads();  // every thread is done with the momenta tile (its space is reused)
   return nvalid;
 }

@@ -83,10 +83,7 @@ def _colour_quadratic(K, ncol) -> list[str]:
 LEAN_SLAB = set(filter(None, os.environ.get("MG_LEAN_SLAB", "ggttgg").split(",")))
 
 
-def emit_gg(n: int, tag: str, mode: str = "straight", half: int | None = None) -> str:
-    """Header of gg -> t t~ + n-2 gluons.  half = 0 / 1: the amplitudes
-    function holds only the first / second half of the scheduled amplitudes
-    (with the currents they need), for the split program."""
+def emit_gg(n: int, tag: str, mode: str = "straight") -> str:
     npar = n + 2
     nhel = 1 << npar
     plan = build_plan(n)
@@ -298,9 +295,6 @@ def emit_gg(n: int, tag: str, mode: str = "straight", half: int | None = None) -
     # in chunked mode)
     group = mode == "chunked" or os.environ.get("MG_LINE_GROUP", "0") == "1"
     amp_order = [i for kind, i in program(plan, by_pattern=True) if kind == "amp"] if group else schedule(plan)
-    if half is not None:
-        cut = len(amp_order) // 2
-        amp_order = amp_order[:cut] if half == 0 else amp_order[cut:]
     pid, psign, pats = colour_patterns(plan)
     last_of = {}
     for ai in amp_order:
@@ -1070,23 +1064,6 @@ CHUNKED = {"ggttggg"}
 CHUNK_AMPS = int(os.environ.get("MG_CHUNK_AMPS", "40"))
 
 
-# processes whose mixed |M|^2 runs the split program: two warps per group of
-# 32 events, each running half of the diagrams (the halves of the liveness
-# schedule, each with the currents it needs) into its own colour flows, which
-# are summed before the colour form; about half the registers per thread
-# (MG_SPLIT: comma-separated tags)
-SPLIT = set(filter(None, os.environ.get("MG_SPLIT", "").split(",")))
-
-_AMP_HEAD = "template <typename R>\n__device__ static __forceinline__ void amplitudes("
-
-
-def _amplitudes_function(src: str) -> str:
-    """The text of the amplitudes function of a generated header."""
-    i0 = src.index(_AMP_HEAD)
-    i1 = src.index("\n}\n", i0) + 3
-    return src[i0:i1]
-
-
 def emit(proc: str) -> tuple[str, str]:
     """(tag, header source) for a process string."""
     tag, n = PROCESSES[proc]
@@ -1098,15 +1075,6 @@ def emit(proc: str) -> tuple[str, str]:
         src = emit_uuttg(tag)
     else:
         src = emit_gg(n, tag, mode="chunked" if tag in CHUNKED else "straight")
-        if tag in SPLIT:
-            assert tag not in CHUNKED
-            halves = []
-            for h in (0, 1):
-                f = _amplitudes_function(emit_gg(n, tag, half=h))
-                halves.append(f.replace("void amplitudes(", f"void amplitudes_half{h}(", 1))
-            end = "};  // struct " + tag
-            assert src.count(end) == 1
-            src = src.replace(end, "// the two halves of the split program\n" + "\n".join(halves) + end)
     return tag, _prepare_in_D(src)
 
 
@@ -1202,8 +1170,6 @@ def emit_tu(proc: str, prec: str) -> tuple[str, str]:
     if prec == "f32":
         if tag in TENSOR_CORE_ROWS:
             mixed = f"launch_sigma_rows<{tag}, {nt32}>(a)"
-        elif tag in SPLIT:
-            mixed = f"launch_sigma_tc_split<{tag}>(a)"
         elif tc:
             mixed = f"launch_sigma_tc<{tag}>(a)"
         else:
