@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # kernel from one ncu capture of the current kernel on a small case: workload
 # -> (events captured, bytes); scaled to a launch by its events (the traffic
 # is per event: momenta in, |M|^2 out).  Set to None when the kernel changes.
-NCU_TRAFFIC = {"ggttgg": (65536, 12.802048e6 + 0.303360e6)}  # sigma_tc_kernel_ggttgg_mixed_65536ev.md (E)
+NCU_TRAFFIC = {"ggttgg": (65536, 12.802048e6 + 0.326912e6)}  # sigma_tc_kernel_ggttgg_mixed_65536ev.md (F)
 
 SERVE_PROCS = {  # process -> sqrt(s)
     "e+ e- > mu+ mu-": 500.0,
