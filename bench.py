@@ -143,14 +143,15 @@ def launches_per_sigma(proc: str, nevt: int, ngood: int) -> int:
 
 
 def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: float = 12.0,
-                one_core: bool = True):
+                one_core: bool = True, max_events: int = 1 << 20):
     """FP64 oracle on the host cores over a bounded sample of the workload's
-    first events: (MEs/s, cores, n, seconds, MEs/s on one core, oracle values)."""
+    first events (at most max_events, the workload's own size): (MEs/s, cores,
+    n, seconds, MEs/s on one core, oracle values)."""
     import oracle as O
     from paper_2303_18244_gb300.inputs import process_momenta
     cores = os.cpu_count() or 1
     O.me(proc, process_momenta(proc, sqrts, cores, seed, first_event))  # colour matrix, warm
-    n = cores
+    n = min(cores, max_events)
     best = None
     while True:
         p = process_momenta(proc, sqrts, n, seed, first_event)
@@ -158,9 +159,9 @@ def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: 
         ref = O.me(proc, p, threads=cores)
         dt = time.perf_counter() - t
         best = (n / dt, cores, n, dt)
-        if dt >= budget_s / 4 or n >= 1 << 20:
+        if dt >= budget_s / 4 or n >= max_events:
             break
-        n = int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3))))
+        n = min(max_events, int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3)))))
     one = None
     if one_core:  # one core, on a sample about two seconds long
         n1 = max(1, min(n, int(best[0] / cores * 2.0)))
@@ -178,9 +179,9 @@ def run_reference(args):
     vals = []
     info = None
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        time_oracle(PROC, SQRTS, SEED, 0, budget_s=2.0, one_core=False)
+        time_oracle(PROC, SQRTS, SEED, 0, budget_s=2.0, one_core=False, max_events=NEVT)
     for _ in range(args.steps):
-        v, cores, n, dt, _, _ = time_oracle(PROC, SQRTS, SEED, 0, budget_s=8.0, one_core=False)
+        v, cores, n, dt, _, _ = time_oracle(PROC, SQRTS, SEED, 0, budget_s=8.0, one_core=False, max_events=NEVT)
         vals.append(v)
         info = (cores, n)
     v = statistics.median(vals)
@@ -373,7 +374,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, n, dt, one, ref = time_oracle(PROC, SQRTS, SEED, first)
+        v, cores, n, dt, one, ref = time_oracle(PROC, SQRTS, SEED, first, max_events=nevt)
         res["cpu_baseline"] = {"value": v, "unit": "MEs/s", "cores": cores, "kind": "oracle",
                                "sample": f"the first {n} events of the workload ({dt:.1f} s wall)",
                                "value_one_core": one}
