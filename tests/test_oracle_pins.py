@@ -394,3 +394,43 @@ def test_uuttg_lorentz_invariance():
     me = O.me("u u~ > t t~ g", p, par)
     q = _boost_rotate(p, [0.3, -0.2, 0.5], [1, 2, 3], 0.7)
     np.testing.assert_allclose(O.me("u u~ > t t~ g", q, par), me, rtol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# Colour-flow weights sum_spins |A(sigma)|^2 (the colour-flow choice)
+# --------------------------------------------------------------------------
+
+def _relabelled(perms, a, b):
+    """Index of each ordering with gluon labels a and b exchanged."""
+    index = {tuple(int(x) for x in s): i for i, s in enumerate(perms)}
+    swap = {a: b, b: a}
+    return np.array([index[tuple(swap.get(int(x), int(x)) for x in s)] for s in perms])
+
+
+@pytest.mark.parametrize("n,nevt", [(2, 10), (3, 6), (4, 3)])
+def test_flow_weights_bose_relabelling(n, nevt):
+    """Exchanging the momenta of two gluons maps the weight of each ordering
+    onto the ordering with those two labels exchanged (a wrong index between
+    orderings and flows fails this)."""
+    proc = PROC_N[n]
+    p = process_momenta(proc, SQRTS[n], nevt, 51)
+    w = O.flow_weights(proc, p)
+    perms = O.permutations(n)
+    assert w.shape == (nevt, len(perms)) and np.all(w >= 0)
+    slots = [0, 1] + list(range(4, n + 2))  # gluon label -> particle slot
+    pairs = [(0, 1)] + ([(2, n - 1)] if n >= 4 else [])
+    for a, b in pairs:
+        q = p.copy()
+        q[:, [slots[a], slots[b]]] = q[:, [slots[b], slots[a]]]
+        np.testing.assert_allclose(O.flow_weights(proc, q), w[:, _relabelled(perms, a, b)], rtol=1e-11)
+
+
+@pytest.mark.parametrize("n,nevt", [(2, 10), (3, 6), (4, 3)])
+def test_flow_weights_lorentz_invariant(n, nevt):
+    """Each ordering's spin-summed |A(sigma)|^2 is Lorentz invariant (Gamma_t = 0)."""
+    proc = PROC_N[n]
+    par = O.Params(wt=0.0)
+    p = process_momenta(proc, SQRTS[n], nevt, 52)
+    w = O.flow_weights(proc, p, par)
+    q = _boost_rotate(p, [0.3, -0.2, 0.5], [1, 2, 3], 0.7)
+    np.testing.assert_allclose(O.flow_weights(proc, q, par), w, rtol=1e-10, atol=1e-12 * w.max())
