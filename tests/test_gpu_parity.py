@@ -381,3 +381,49 @@ def test_element_offsets_beyond_32_bits(proc, precision, nevt):
     else:
         r = _rel(got, ref)
         assert np.median(r) <= 1e-5 and r.max() <= 1e-2
+
+
+def _rotate_onto_axis(p, slot, sign):
+    """Rotate every final-state momentum of each event so that particle `slot`
+    points along sign * z, then set its transverse components to exactly 0
+    (and, for two-body final states, its partner's to the exact opposite)."""
+    q = p.copy()
+    target = np.array([0.0, 0.0, float(sign)])
+    for e in range(q.shape[0]):
+        t = q[e, slot, 1:] / np.linalg.norm(q[e, slot, 1:])
+        axis = np.cross(t, target)
+        s, c = np.linalg.norm(axis), float(t @ target)
+        if s > 0:
+            k = axis / s
+            K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+            R = np.eye(3) + s * K + (1 - c) * K @ K
+            q[e, 2:, 1:] = q[e, 2:, 1:] @ R.T
+        P = np.linalg.norm(q[e, slot, 1:])
+        q[e, slot, 1:] = [0.0, 0.0, sign * P]
+        if q.shape[1] == 4:
+            q[e, 5 - slot, 1:] = [0.0, 0.0, -sign * P]
+    return q
+
+
+@pytest.mark.parametrize("proc", [p for p in PROCS if p != "g g > t t~ g g g"], ids=_ids)
+def test_final_state_along_the_beam_axis(proc):
+    """Special kinematics: the top (mu- for e+e- -> mu+mu-) exactly along +z
+    and along -z (p_T = 0), where the spinor set-up takes its degenerate
+    branch (p along -z) and the azimuth is undefined; FP64 within 1e-12 of the
+    oracle, mixed within its bounds, no NaN.  (Gluons are never put on the
+    axis: that is the collinear singularity with a beam gluon.)"""
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, _, _ = WORKLOADS[proc]
+    slot = 3 if proc == "e+ e- > mu+ mu-" else 2
+    base = process_momenta(proc, rs, 8, seed + 3000)
+    p = np.concatenate([_rotate_onto_axis(base, slot, +1), _rotate_onto_axis(base, slot, -1)])
+    assert np.all(p[:, slot, 1:3] == 0.0)
+    ref = O.me(proc, p)
+    assert np.all(np.isfinite(ref)) and np.all(ref > 0)
+    got = _gpu_me(mg.Process(proc), p)
+    assert np.all(np.isfinite(got))
+    _assert_fp64(proc, p, got, ref)
+    mixed = _gpu_me(mg.Process(proc, precision=mg.MG_MIXED), p)
+    r = _rel(mixed, ref)
+    assert np.all(np.isfinite(mixed)) and np.median(r) <= 1e-5 and r.max() <= 1e-2
