@@ -96,3 +96,16 @@ def test_two_line_decomposition_closed_form():
     for d, row in enumerate(rows):
         assert row[0] == f"D{d + 1}"
         assert [tuple(c) for c in got[d]] == [_cfrac(t) for t in row[1:]], row[0]
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_colour_matrix_constant_row_sums(n):
+    """Relabelling the gluons permutes the orderings and leaves C invariant, so
+    every row of C has the same sum (the all-ones vector is an eigenvector);
+    for three gluons it is the sum of the six classes, 60/9."""
+    C = O.colour_matrix(n).real
+    rows = C.sum(1)
+    np.testing.assert_allclose(rows, rows[0], rtol=1e-13)
+    if n == 3:
+        table = _sections()["one_line_three_gluons"]
+        assert abs(rows[0] - sum(int(r[1]) for r in table) / 9) < 1e-13
