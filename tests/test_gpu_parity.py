@@ -427,3 +427,27 @@ def test_final_state_along_the_beam_axis(proc):
     mixed = _gpu_me(mg.Process(proc, precision=mg.MG_MIXED), p)
     r = _rel(mixed, ref)
     assert np.all(np.isfinite(mixed)) and np.median(r) <= 1e-5 and r.max() <= 1e-2
+
+
+@pytest.mark.parametrize("proc,precision", [
+    ("e+ e- > mu+ mu-", mg.MG_FP64), ("g g > t t~", mg.MG_MIXED),
+    ("g g > t t~ g g", mg.MG_FP64), ("g g > t t~ g g", mg.MG_MIXED),
+], ids=["eemumu-fp64", "ggtt-mixed", "ggttgg-fp64", "ggttgg-mixed"])
+def test_nan_event_stays_in_its_lane(proc, precision):
+    """Bad input is not an error of the call: an event with NaN momenta gets a
+    NaN |M|^2 and every other event of the batch (the same CTA included, and
+    the tensor-core colour form, whose rows are independent) is bit-identical
+    to the clean batch; the handle reports no error."""
+    if not _have(proc):
+        pytest.fail(f"{proc} is not compiled into libmg.so")
+    rs, seed, _, _ = WORKLOADS[proc]
+    p = process_momenta(proc, rs, 300, seed + 4000)
+    h = mg.Process(proc, precision=precision)
+    clean = _gpu_me(h, p)
+    bad = p.copy()
+    bad[5, 2, 1] = np.nan
+    bad[200] = np.nan
+    got = _gpu_me(h, bad)
+    assert np.isnan(got[5]) and np.isnan(got[200])
+    keep = np.setdiff1d(np.arange(300), [5, 200])
+    np.testing.assert_array_equal(got[keep], clean[keep])
