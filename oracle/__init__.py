@@ -52,6 +52,11 @@ class Params:
         return np.array(astuple(self), dtype=np.float64)
 
 
+# plain C11; no contraction into FMAs, so that every product and sum is
+# rounded as written
+CFLAGS = ["-std=gnu11", "-O2", "-fPIC", "-shared", "-fcx-limited-range", "-ffp-contract=off"]
+
+
 def build(force: bool = False) -> str:
     """Compile mg_oracle.c with gcc (plain C11): the FP64 oracle and its
     extended-precision twin (same source, long double arithmetic)."""
@@ -61,8 +66,7 @@ def build(force: bool = False) -> str:
                 and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC)):
             continue
         tmp = lib_path + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-fcx-limited-range", "-ffp-contract=off",
-               *extra, "-o", tmp, _SRC, "-lm", "-lpthread"]
+        cmd = ["gcc", *CFLAGS, *extra, "-o", tmp, _SRC, "-lm", "-lpthread"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, lib_path)
     return _LIB
