@@ -66,7 +66,7 @@ def test_diagram_counts(n, want):
     assert diagrams.count_diagrams(n) == want
 
 
-@pytest.mark.parametrize("proc,n", [("g g > t t~", 2), ("g g > t t~ g", 3), ("g g > t t~ g g", 4)])
+@pytest.mark.parametrize("proc,n", [("g g > t t~", 2), ("g g > t t~ g", 3), ("g g > t t~ g g", 4), ("g g > t t~ g g g", 5)])
 def test_amplitude_terms_and_header_constants(proc, n):
     """The generated header's NDIAG and NAMP (terms: a four-gluon vertex
     counts three times) equal the recursion's counts."""
