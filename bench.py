@@ -142,6 +142,16 @@ def launches_per_sigma(proc: str, nevt: int, ngood: int) -> int:
     return 2 * ((ngood + hs - 1) // hs)
 
 
+def measured_hbm_gbs():
+    """The measured copy bandwidth of this machine's GPUs (GB/s), or None."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: float = 12.0,
                 one_core: bool = True, max_events: int = 1 << 20):
     """FP64 oracle on the host cores over a bounded sample of the workload's
@@ -245,9 +255,10 @@ def main():
     ngood, _ = mg.good_helicities(hmix, torch.from_numpy(calib).cuda())
     mg.good_helicities(h64, torch.from_numpy(calib).cuda())
 
-    def timed(h, o, steps, warmup):
+    def timed_call(fn, steps, warmup):
+        """CUDA-event times (ms) of fn() on the stream, L2 flushed before each."""
         for _ in range(warmup):
-            mg.sigma(h, mom, o, stream)
+            fn()
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -257,13 +268,16 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            mg.sigma(h, mom, o, stream)
+            fn()
             e1.record(stream)
             per.append((e0, e1))
         torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in per]
         barrier()
         return ms
+
+    def timed(h, o, steps, warmup):
+        return timed_call(lambda: mg.sigma(h, mom, o, stream), steps, warmup)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -330,6 +344,38 @@ def main():
         dev_ms.append((time.perf_counter() - t0) * 1e3)
     dev_t = max_over_ranks([statistics.median(dev_ms)], device="cuda")[0]
 
+    # the ME with the event-by-event choice of a good helicity and a colour
+    # flow (mg_sigma_select, mixed: colour sum on CUDA cores), on the same events
+    from paper_2303_18244_gb300.inputs import uniforms
+    rnd = torch.from_numpy(np.ascontiguousarray(uniforms(SEED + 2000, first, nevt, 1)[:, 0, :2])).cuda()
+    hel_o = torch.empty(nevt, dtype=torch.int32, device="cuda")
+    col_o = torch.empty(nevt, dtype=torch.int32, device="cuda")
+    out_s = torch.empty(nevt, dtype=torch.float64, device="cuda")
+    ms_sel = timed_call(lambda: mg.sigma_select(hmix, mom, rnd, out_s, hel_o, col_o, None, stream), 2, 1)
+    assert mg.process_status(hmix) == 0
+    t_sel = max_over_ranks([statistics.median(ms_sel)], device="cuda")[0]
+
+    # hit-or-miss unweighting (mg_unweight) of the workload's MEs, and of
+    # 128 copies of them (67 M events, 1 GiB of weights and uniforms: HBM-bound)
+    def unweight_ms(w, r):
+        idx = torch.empty(w.shape[0], dtype=torch.int64, device="cuda")
+        nacc = torch.empty(1, dtype=torch.int64, device="cuda")
+        wmax = float(w.max())
+        ms_u = timed_call(lambda: mg.unweight(w, r, wmax, idx, nacc, stream), 3, 2)
+        return statistics.median(ms_u), int(nacc.item())
+    r_u = rnd[:, 0].contiguous()
+    uw_ms, uw_kept = unweight_ms(out, r_u)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(SEED + 3000)
+    w_big = out.repeat(128)
+    r_big = torch.rand(w_big.shape[0], dtype=torch.float64, device="cuda", generator=gen)
+    uwb_ms, uwb_kept = unweight_ms(w_big, r_big)
+    del w_big, r_big
+    uw_t, uwb_t = max_over_ranks([uw_ms, uwb_ms], device="cuda")
+    hbm_peak = measured_hbm_gbs()
+    # algorithmic bytes: w and r read once (16 B per event), 8 B per kept index
+    uwb_bytes = 16 * 128 * nevt + 8 * uwb_kept
+
     fl = load_flops(args.proc)
     flops_evt = ngood * (fl["amp_flops_per_hel"] + fl["colour_dense_flops_per_hel"])
     kernel_ms = t_mix / args.steps
@@ -370,6 +416,18 @@ def main():
                      "kernel": f"sigma kernel of {args.proc}, mixed",
                      "flops_per_event": flops_evt,
                      "peak_source": "measured FP32 FMA loop (mg_diag), burst"},
+        "select": {"value": world * nevt / (t_sel * 1e-3), "unit": "MEs/s",
+                   "what": "mg_sigma_select, mixed: the ME plus a good helicity and a colour flow per event "
+                           "(colour sum on CUDA cores)"},
+        "unweight": {"value": world * nevt / (uw_t * 1e-3), "unit": "events/s", "ms": uw_t, "kept": uw_kept,
+                     "what": "mg_unweight of the workload's MEs (hit-or-miss, kept indices in order)",
+                     "large": {"events": 128 * nevt, "ms": uwb_t, "kept": uwb_kept,
+                               "roofline": {"bound": "hbm", "achieved": uwb_bytes / (uwb_t * 1e-3) / 1e9,
+                                            "peak": hbm_peak, "unit": "GB/s",
+                                            "frac": (uwb_bytes / (uwb_t * 1e-3) / 1e9) / hbm_peak
+                                            if hbm_peak else None,
+                                            "bytes_per_event": "16 read (w, r) + 8 per kept index",
+                                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)"}}},
         "gpu_launches": args.steps * launches_per_sigma(args.proc, nevt, ngood),
         "clocks": clk,
     }

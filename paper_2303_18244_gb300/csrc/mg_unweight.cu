@@ -5,9 +5,12 @@
 // that follow the matrix element in the event generator, and names it as a
 // candidate to offload to the GPU.  Event i is kept when r_i * w_max < w_i
 // (r_i uniform in [0, 1)); the kept indices are written in increasing order,
-// so the result does not depend on the launch configuration.  Three launches: per-tile counts, one scan of
-// the tile counts, then each tile ranks its kept events (warp ballots and a
-// block scan) and writes them at its tile's offset.
+// so the result does not depend on the launch configuration.  Three launches:
+// per tile of 2048 events, the accept bits (one warp ballot per 32 events,
+// n/8 bytes in all) and their count; one scan of the tile counts; then each
+// tile ranks its kept events from its bits alone and writes their indices at
+// its tile's offset.  w and r are read once: 16 bytes per event, plus 8 per
+// kept index.
 #include <cuda_runtime.h>
 
 #include "mg.h"
@@ -17,99 +20,106 @@ namespace {
 constexpr int UW_THREADS = 256;
 constexpr int UW_PER_THREAD = 8;
 constexpr int UW_TILE = UW_THREADS * UW_PER_THREAD;  // events per tile
+constexpr int UW_WARPS = UW_THREADS / 32;
+constexpr int UW_WORDS = UW_PER_THREAD * UW_WARPS;  // accept-bit words per tile
 
 __device__ __forceinline__ bool kept(const double* __restrict__ w, const double* __restrict__ r, double w_max,
                                      long long i) {
   return r[i] * w_max < w[i];
 }
 
-// Events of tile b handled by thread t: b*TILE + j*THREADS + t (coalesced).
+// Pass 1.  Thread t of tile b takes events b*TILE + j*THREADS + t, j < PER_THREAD
+// (coalesced); word j*WARPS + warp of the tile's bits holds the ballot of
+// events b*TILE + j*THREADS + warp*32 + lane, so the words in order cover the
+// tile in increasing index order.
 __global__ void __launch_bounds__(UW_THREADS)
     tile_count_kernel(const double* __restrict__ w, const double* __restrict__ r, long long n, double w_max,
-                      long long* __restrict__ counts) {
-  __shared__ int warp_sum[UW_THREADS / 32];
+                      long long* __restrict__ counts, unsigned* __restrict__ bits) {
+  __shared__ int warp_sum[UW_WARPS];
   const long long base = (long long)blockIdx.x * UW_TILE;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned* tb = bits + (long long)blockIdx.x * UW_WORDS;
   int c = 0;
 #pragma unroll
   for (int j = 0; j < UW_PER_THREAD; j++) {
     const long long i = base + j * UW_THREADS + threadIdx.x;
-    if (i < n && kept(w, r, w_max, i)) c++;
+    const unsigned m = __ballot_sync(0xffffffffu, i < n && kept(w, r, w_max, i));
+    if (lane == 0) tb[j * UW_WARPS + warp] = m;
+    c += __popc(m);  // the same in every lane of the warp
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+  if (lane == 0) warp_sum[warp] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
-    long long s = 0;
-    for (int k = 0; k < UW_THREADS / 32; k++) s += warp_sum[k];
-    counts[blockIdx.x] = s;
+    long long t = 0;
+    for (int k = 0; k < UW_WARPS; k++) t += warp_sum[k];
+    counts[blockIdx.x] = t;
   }
 }
 
-// Exclusive scan of the tile counts in place (one block); total into *n_acc.
+// Pass 2: exclusive scan of the tile counts in place (one block: each thread
+// sums a contiguous run of tiles, one block scan of the run sums, each thread
+// rewrites its run); the total into *n_acc.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(long long* __restrict__ counts, long long ntiles,
                                                          long long* __restrict__ n_acc) {
   __shared__ long long part[1024];
-  __shared__ long long carry;
-  if (threadIdx.x == 0) carry = 0;
+  const int t = threadIdx.x;
+  const long long per = (ntiles + 1023) / 1024;
+  const long long b0 = t * per;
+  const long long b1 = b0 + per < ntiles ? b0 + per : ntiles;
+  long long own = 0;
+  for (long long b = b0; b < b1; b++) own += counts[b];
+  part[t] = own;
   __syncthreads();
-  for (long long b0 = 0; b0 < ntiles; b0 += 1024) {
-    const long long b = b0 + threadIdx.x;
-    const long long v = b < ntiles ? counts[b] : 0;
-    part[threadIdx.x] = v;
+  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+    const long long add = t >= o ? part[t - o] : 0;
     __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 values
-    for (int o = 1; o < 1024; o <<= 1) {
-      const long long add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-      __syncthreads();
-      part[threadIdx.x] += add;
-      __syncthreads();
-    }
-    if (b < ntiles) counts[b] = carry + part[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
+    part[t] += add;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *n_acc = carry;
+  long long run = part[t] - own;
+  for (long long b = b0; b < b1; b++) {
+    const long long v = counts[b];
+    counts[b] = run;
+    run += v;
+  }
+  if (t == 1023) *n_acc = part[1023];
 }
 
+// Pass 3: from the tile's bits only, each kept event's rank in the tile (the
+// counts of the words before its word, then the bits below its lane) and its
+// index at the tile's offset.
 __global__ void __launch_bounds__(UW_THREADS)
-    tile_write_kernel(const double* __restrict__ w, const double* __restrict__ r, long long n, double w_max,
-                      const long long* __restrict__ offsets, long long* __restrict__ idx_out) {
-  __shared__ int warp_tot[UW_PER_THREAD][UW_THREADS / 32];
-  __shared__ long long row_base[UW_PER_THREAD];
+    tile_write_kernel(const unsigned* __restrict__ bits, const long long* __restrict__ offsets,
+                      long long* __restrict__ idx_out) {
+  static_assert(UW_WORDS == 64, "two words per lane in the word scan");
+  __shared__ int word_excl[UW_WORDS];
   const long long base = (long long)blockIdx.x * UW_TILE;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  bool k[UW_PER_THREAD];
-  int rank_in_warp[UW_PER_THREAD];
+  const unsigned* tb = bits + (long long)blockIdx.x * UW_WORDS;
+  if (warp == 0) {
+    const int c0 = __popc(tb[lane]), c1 = __popc(tb[32 + lane]);
+    int s0 = c0, s1 = c1;
 #pragma unroll
-  for (int j = 0; j < UW_PER_THREAD; j++) {
-    const long long i = base + j * UW_THREADS + threadIdx.x;
-    k[j] = i < n && kept(w, r, w_max, i);
-    const unsigned m = __ballot_sync(0xffffffffu, k[j]);
-    rank_in_warp[j] = __popc(m & ((1u << lane) - 1u));
-    if (lane == 0) warp_tot[j][warp] = __popc(m);
-  }
-  __syncthreads();
-  // rows j in increasing index order: row j covers events base + j*THREADS .. +THREADS-1
-  if (threadIdx.x == 0) {
-    long long s = offsets[blockIdx.x];
-    for (int j = 0; j < UW_PER_THREAD; j++) {
-      row_base[j] = s;
-      for (int q = 0; q < UW_THREADS / 32; q++) {
-        const int t = warp_tot[j][q];
-        warp_tot[j][q] = (int)(s - row_base[j]);  // exclusive prefix within the row
-        s += t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a0 = __shfl_up_sync(0xffffffffu, s0, o);
+      const int a1 = __shfl_up_sync(0xffffffffu, s1, o);
+      if (lane >= o) {
+        s0 += a0;
+        s1 += a1;
       }
     }
+    const int tot0 = __shfl_sync(0xffffffffu, s0, 31);
+    word_excl[lane] = s0 - c0;
+    word_excl[32 + lane] = tot0 + s1 - c1;
   }
   __syncthreads();
+  const long long off = offsets[blockIdx.x];
 #pragma unroll
   for (int j = 0; j < UW_PER_THREAD; j++) {
-    if (k[j]) {
-      const long long i = base + j * UW_THREADS + threadIdx.x;
-      idx_out[row_base[j] + warp_tot[j][warp] + rank_in_warp[j]] = i;
-    }
+    const int q = j * UW_WARPS + warp;
+    const unsigned m = tb[q];
+    if ((m >> lane) & 1u)
+      idx_out[off + word_excl[q] + __popc(m & ((1u << lane) - 1u))] = base + j * UW_THREADS + threadIdx.x;
   }
 }
 
@@ -123,13 +133,14 @@ extern "C" int mg_unweight(const double* w_dev, const double* r_dev, int64_t n, 
   if (!w_dev || !r_dev || !idx_out_dev) return MG_ERR_ARG;
   const long long ntiles = (n + UW_TILE - 1) / UW_TILE;
   if (ntiles > 0x7fffffffLL) return MG_ERR_ARG;
+  // workspace: the tile counts (then offsets), then the accept bits
   long long* counts = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&counts), sizeof(long long) * ntiles, s) != cudaSuccess)
-    return MG_ERR_NOMEM;
-  tile_count_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(w_dev, r_dev, n, w_max, counts);
+  const size_t bytes = (size_t)ntiles * (sizeof(long long) + UW_WORDS * sizeof(unsigned));
+  if (cudaMallocAsync(reinterpret_cast<void**>(&counts), bytes, s) != cudaSuccess) return MG_ERR_NOMEM;
+  unsigned* bits = reinterpret_cast<unsigned*>(counts + ntiles);
+  tile_count_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(w_dev, r_dev, n, w_max, counts, bits);
   tile_scan_kernel<<<1, 1024, 0, s>>>(counts, ntiles, reinterpret_cast<long long*>(n_acc_dev));
-  tile_write_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(w_dev, r_dev, n, w_max, counts,
-                                                            reinterpret_cast<long long*>(idx_out_dev));
+  tile_write_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(bits, counts, reinterpret_cast<long long*>(idx_out_dev));
   const cudaError_t e1 = cudaGetLastError();
   const cudaError_t e2 = cudaFreeAsync(counts, s);
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? MG_OK : MG_ERR_CUDA;
