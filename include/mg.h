@@ -241,8 +241,11 @@ int mg_server_create(const mg_server_cfg* cfg, mg_server** out);
 /* Queue a request: nevt events momenta[nevt][npar][4] (host memory), results
  * written to me_out[nevt] (host memory) before the request completes.  Both
  * buffers are the caller's and must stay valid until mg_server_poll has
- * returned MG_OK or an error for the request.  Non-blocking.  A request larger
- * than the memory budget can never be admitted: MG_ERR_NOMEM at submit. */
+ * returned MG_OK or an error for the request, and so must the process handle
+ * h (it may be destroyed after that; the graphs the server captured for it
+ * are keyed by the handle's own serial number and are not replayed for a
+ * later handle).  Non-blocking.  A request larger than the memory budget can
+ * never be admitted: MG_ERR_NOMEM at submit. */
 int mg_server_submit(mg_server* s, mg_process* h, const double* momenta, int64_t nevt, double* me_out,
                      uint64_t* req_id);
 

@@ -2,6 +2,7 @@
 // filter, per-event ME launches from device or host buffers.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -105,6 +106,10 @@ extern "C" int mg_process_create(const char* proc, const mg_params* p, mg_proces
   if (rc) return rc;
   mg_process* h = new (std::nothrow) mg_process();
   if (!h) return MG_ERR_NOMEM;
+  // a serial number that no later handle reuses, even at the same address
+  // (the server keys its captured graphs by it)
+  static std::atomic<uint64_t> next_serial{1};
+  h->serial = next_serial.fetch_add(1);
   h->d = d;
   h->par = *p;
   h->kp = kp;

@@ -10,6 +10,7 @@
 #include "mg_kernels.cuh"
 
 struct mg_process {
+  uint64_t serial = 0;              // unique per handle created in this process (never reused)
   const mg::ProcDesc* d = nullptr;
   mg_params par{};
   mg::KParams kp{};

@@ -10,7 +10,9 @@
 //   - a chunk is admitted to one of n_streams device slots when a slot is free
 //     and the in-flight device bytes stay within mem_budget_bytes;
 //   - per slot: H2D copy, padding kernel, the sigma launch replayed from a
-//     CUDA graph captured once per (slot, process, bucket, helicity list),
+//     CUDA graph captured once per (slot, process handle, bucket, helicity
+//     list) -- the handle by its serial number, never reused, so a graph is
+//     never replayed for a later handle that reuses a destroyed one's address,
 //     D2H copy, completion event -- so chunks that arrive while others run
 //     overlap on the device;
 //   - completions are observed by polling the slots' events; a request is done
@@ -84,7 +86,7 @@ struct mg_server {
   std::vector<Slot> slots;
   std::deque<Chunk> queue;
   std::unordered_map<uint64_t, Request*> reqs;
-  std::map<std::tuple<int, mg_process*, int64_t, unsigned>, cudaGraphExec_t> graphs;
+  std::map<std::tuple<int, uint64_t, int64_t, unsigned>, cudaGraphExec_t> graphs;
   std::mutex m;
   std::condition_variable cv_work, cv_done;
   std::thread th;
@@ -126,7 +128,7 @@ int mg_server::admit(int si, const Chunk& c) {
       std::lock_guard<std::mutex> lk(h->lock);
       ver = h->hel_version;
     }
-    auto key = std::make_tuple(si, h, c.bucket, ver);
+    auto key = std::make_tuple(si, h->serial, c.bucket, ver);
     auto it = graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it == graphs.end()) {

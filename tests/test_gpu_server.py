@@ -101,3 +101,22 @@ def test_zero_event_request():
     rc, st = srv.poll(rid, 1_000_000)
     assert rc == mg.MG_OK and st.nevt == 0
     srv.close()
+
+
+def test_new_handles_after_destroyed_ones():
+    """Handles destroyed once their requests completed, and new ones created
+    (the allocator often hands out the freed address again): each request
+    runs its own handle's process and constants, never a graph the server
+    captured for an earlier handle."""
+    srv = mg.Server(n_streams=1, min_bucket=256, max_bucket=1024)
+    cases = [("g g > t t~", process_momenta("g g > t t~", 1000.0, 300, 5)),
+             ("g g > t t~ g", process_momenta("g g > t t~ g", 1200.0, 300, 6))]
+    for _ in range(3):
+        for proc, mom in cases:
+            h = mg.Process(proc)
+            o = np.full(mom.shape[0], np.nan)
+            rc, st = srv.poll(srv.submit(h, mom, o), 60_000_000)
+            assert rc == mg.MG_OK and st.status == 0
+            np.testing.assert_array_equal(o, _alone(h, mom))
+            h.close()
+    srv.close()
