@@ -203,8 +203,12 @@ int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, 
   a.mom = mom;
   a.nevt = nevt;
   a.out = me;
-  a.hels = h->d_hels;
-  a.nhel = h->n_good;
+  {
+    // the list and its length together (mg_good_helicities may replace them)
+    std::lock_guard<std::mutex> lk(h->lock);
+    a.hels = h->d_hels;
+    a.nhel = h->n_good;
+  }
   a.kp = h->kp;
   a.ctile = h->d_ctile;
   a.status = h->d_status;
@@ -236,8 +240,11 @@ extern "C" int mg_sigma_select(mg_process* h, const double* momenta_dev, int64_t
   a.mom = momenta_dev;
   a.nevt = nevt;
   a.out = me_out_dev;
-  a.hels = h->d_hels;
-  a.nhel = h->n_good;
+  {
+    std::lock_guard<std::mutex> lk(h->lock);
+    a.hels = h->d_hels;
+    a.nhel = h->n_good;
+  }
   a.kp = h->kp;
   a.status = h->d_status;
   a.stream = static_cast<cudaStream_t>(stream);
