@@ -65,3 +65,17 @@ def test_host_only_calls(libmg):
     h = ctypes.c_void_p()
     assert libmg.mg_process_create(b"g g > t t~", None, ctypes.byref(h)) == -2
     assert libmg.mg_process_info(None, None, None, None, None, None) == -2
+
+
+def test_no_cpu_fallback_without_a_gpu(libmg):
+    """The product path has no CPU fallback: without a CUDA device a process
+    handle cannot be created (a CUDA error, not a silent CPU result), and the
+    binding refuses host tensors where device buffers are required."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("checks the behaviour on a machine without a GPU")
+    with pytest.raises(mg.MGError) as ei:
+        mg.Process("g g > t t~")
+    assert ei.value.code in (-3, -4)  # MG_ERR_NOMEM / MG_ERR_CUDA
+    with pytest.raises(TypeError):
+        mg._dev_check(torch.zeros((8, 4, 4), dtype=torch.float64))
