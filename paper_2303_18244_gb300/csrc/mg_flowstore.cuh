@@ -55,7 +55,9 @@ struct FlowsSmem {
 struct FlowsTmem {
   uint32_t taddr;  // lane (bits 16-31) and first column of the thread's flows
   __device__ __forceinline__ void chunk_done() const {
+#ifdef __CUDA_ARCH__
     if constexpr (MG_CHUNK_SYNC != 0) __syncthreads();
+#endif
   }
   template <int N>
   __device__ __forceinline__ void update(const int (&k)[N], const int (&sg)[N], cx<float> v) const {
@@ -138,7 +140,9 @@ struct FlowsTmem {
 struct FlowsTmem64 {
   uint32_t taddr;
   __device__ __forceinline__ void chunk_done() const {
+#ifdef __CUDA_ARCH__
     if constexpr (MG_CHUNK_SYNC != 0) __syncthreads();
+#endif
   }
   template <int N>
   __device__ __forceinline__ void update(const int (&k)[N], const int (&sg)[N], cx<double> v) const {
