@@ -88,6 +88,27 @@ def _couplings(proc):
     return [math.sqrt(4.0 * math.pi * par.alpha_s), par.mt, par.wt, 0.0, 0.0, 0.0, 0.0, 0.0]
 
 
+def host_me(proc, real, workdir, header=None, vertices=None):
+    """(momenta, |M|^2) of the generated code of proc compiled for the host
+    in workdir; header / vertices replace the generated header or the text of
+    mg_vertices.cuh (a copy in workdir is found before the original)."""
+    tag, generated = emit.emit(proc)
+    (workdir / f"{tag}.cuh").write_text(generated if header is None else header)
+    if vertices is not None:
+        (workdir / "mg_vertices.cuh").write_text(vertices)
+    src = workdir / "main.cpp"
+    src.write_text(PROGRAM.replace("TAG", tag))
+    exe = workdir / "main"
+    subprocess.run(["g++", "-O0", "-std=c++17", f"-DREAL={real}", f"-I{workdir}", f"-I{CSRC}", "-o", str(exe),
+                    str(src)], check=True)
+    sqrts, n = CASES[proc]
+    p = process_momenta(proc, sqrts, n, 91)
+    lines = [" ".join(repr(float(x)) for x in _couplings(proc)), str(n)]
+    lines += [" ".join(repr(float(x)) for x in ev.ravel()) for ev in p]
+    out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    return p, np.array([float(x) for x in out.stdout.split()])
+
+
 @pytest.mark.parametrize("real", ["double", "float"], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("proc", list(CASES), ids=lambda p: emit.PROCESSES[p][0])
 def test_generated_code_on_the_host_matches_the_oracle(proc, real, tmp_path):
@@ -95,19 +116,8 @@ def test_generated_code_on_the_host_matches_the_oracle(proc, real, tmp_path):
     and helicity sum (what the mixed kernels run, with the colour form on
     CUDA cores in place of the tensor cores): the mixed bounds of the GPU
     parity tests."""
-    tag, header = emit.emit(proc)
-    (tmp_path / f"{tag}.cuh").write_text(header)
-    src = tmp_path / "main.cpp"
-    src.write_text(PROGRAM.replace("TAG", tag))
-    exe = tmp_path / "main"
-    subprocess.run(["g++", "-O0", "-std=c++17", f"-DREAL={real}", f"-I{tmp_path}", f"-I{CSRC}", "-o", str(exe),
-                    str(src)], check=True)
-    sqrts, n = CASES[proc]
-    p = process_momenta(proc, sqrts, n, 91)
-    lines = [" ".join(repr(float(x)) for x in _couplings(proc)), str(n)]
-    lines += [" ".join(repr(float(x)) for x in ev.ravel()) for ev in p]
-    out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
-    got = np.array([float(x) for x in out.stdout.split()])
+    p, got = host_me(proc, real, tmp_path)
+    n = CASES[proc][1]
     assert got.shape == (n,) and np.all(np.isfinite(got))
     ref = O.me(proc, p)
     r = np.abs(got - ref) / np.abs(ref)
