@@ -128,3 +128,19 @@ def test_generated_code_on_the_host_matches_the_oracle(proc, real, tmp_path):
     if bad.size:  # the long-double oracle decides, as for the GPU's FP64 path
         ext = O.me(proc, p[bad], extended=True)
         assert np.max(np.abs(got[bad] - ext) / np.abs(ext)) <= 1e-12
+
+
+def test_shared_current_chunk_order(tmp_path, monkeypatch):
+    """gg -> t t~ g g g with the chunks ordered by shared currents
+    (MG_CHUNK_ORDER=shared, not the default): a store of 87 crossing currents
+    instead of 241, and the same |M|^2 (FP64, within 1e-12 of the oracle)."""
+    import re
+    proc = "g g > t t~ g g g"
+    _, default = emit.emit(proc)
+    monkeypatch.setenv("MG_CHUNK_ORDER", "shared")
+    _, shared = emit.emit(proc)
+    store = [int(re.search(r"NSTORE = (\d+)", src).group(1)) for src in (default, shared)]
+    assert store == [241, 87]
+    p, got = host_me(proc, "double", tmp_path, header=shared)
+    ref = O.me(proc, p)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-12
