@@ -55,6 +55,15 @@ MUTANTS = [
     ("u u~ -> t t~ g: three-gluon vertex momentum term reversed",
      "y[mu] = p5[mu] - q34[mu];", "y[mu] = q34[mu] - p5[mu];",
      P.test_uuttg_ward_identity),
+    ("identical-particle factor loop off by one",
+     "for (int i = 2; i <= n - 2; i++) iden *= i;", "for (int i = 2; i <= n - 1; i++) iden *= i;",
+     lambda: P.test_spin_colour_summed_me_and_normalisation(3, 61)),
+    ("top and antitop spin states read from the same helicity bit",
+     "const int st = (h >> n) & 1, stb = (h >> (n + 1)) & 1;", "const int st = (h >> n) & 1, stb = (h >> n) & 1;",
+     lambda: P.test_spin_colour_summed_me_and_normalisation(3, 61)),
+    ("a gluon's polarisation state read from its neighbour's helicity bit",
+     "q.eps[i][mu] = pol[i][(h >> i) & 1][mu];", "q.eps[i][mu] = pol[i][(h >> (i + 1)) & 1][mu];",
+     lambda: P.test_spin_colour_summed_me_and_normalisation(3, 61)),
 ]
 
 

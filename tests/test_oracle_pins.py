@@ -16,7 +16,9 @@ mg_oracle.c fails at least one of them:
   relative to the quark-gluon vertex.
 * Colour decomposition: colour-dressed recursion with explicit f^{abc},
   summed over all colour assignments, equals A^dagger C A (2..4 gluons).
-* Full ME: Bose symmetry and Lorentz invariance.
+* Full ME: Bose symmetry and Lorentz invariance; the spin and colour sum
+  rebuilt over every spin state of a helicity basis built in the test, with
+  the identical-particle factor counted from Bose symmetry (3..5 gluons).
 """
 import math
 
@@ -434,3 +436,102 @@ def test_flow_weights_lorentz_invariant(n, nevt):
     w = O.flow_weights(proc, p, par)
     q = _boost_rotate(p, [0.3, -0.2, 0.5], [1, 2, 3], 0.7)
     np.testing.assert_allclose(O.flow_weights(proc, q, par), w, rtol=1e-10, atol=1e-12 * w.max())
+
+
+# --------------------------------------------------------------------------
+# The full spin- and colour-summed ME and its normalisation
+# --------------------------------------------------------------------------
+
+def _helicity_spinors(p, m):
+    """Massive Dirac-representation spinors in the helicity basis, built here
+    from the eigenvectors of sigma.p_hat (a basis other than the oracle's
+    spin-z one, with arbitrary phases): u = [sqrt(E+m) chi; s sqrt(E-m) chi],
+    v = [s sqrt(E-m) eta; sqrt(E+m) eta], s = +-1 the helicity sign."""
+    k = p[1:] / np.linalg.norm(p[1:])
+    sp = np.array([[k[2], k[0] - 1j * k[1]], [k[0] + 1j * k[1], -k[2]]])
+    val, vec = np.linalg.eigh(sp)
+    a, b = math.sqrt(p[0] + m), math.sqrt(max(p[0] - m, 0.0))
+    us, vs = [], []
+    for j, phase in enumerate((np.exp(0.3j), np.exp(-1.1j))):
+        chi = vec[:, j] * phase
+        s = round(val[j])
+        us.append(np.concatenate([a * chi, s * b * chi]))
+        vs.append(np.concatenate([s * b * chi, a * chi]))
+    return us, vs
+
+
+def _circular_polarisations(p, outgoing):
+    """eps+- = (e1 +- i e2)/sqrt(2) with e1 from a fixed oblique reference
+    direction (not the oracle's coordinate-axis construction); conjugated for
+    an outgoing gluon."""
+    k = p[1:] / np.linalg.norm(p[1:])
+    ref = np.array([0.36, -0.48, 0.8])
+    e1 = np.cross(ref, k)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(k, e1)
+    out = []
+    for sgn in (1, -1):
+        e = np.concatenate([[0.0], (e1 + sgn * 1j * e2) / math.sqrt(2)])
+        out.append(e.conj() if outgoing else e)
+    return out
+
+
+def _final_gluon_symmetry(proc, p, n):
+    """How many permutations of the final-state gluons' momenta leave |M|^2
+    unchanged (Bose symmetry: all of them, for generic momenta).  The top and
+    antitop are distinct particles and are not permuted (their exchange is a
+    charge conjugation, which also leaves the summed |M|^2 unchanged)."""
+    import itertools
+    me0 = O.me(proc, p[None])[0]
+    final = list(range(4, n + 2))
+    count = 0
+    for perm in itertools.permutations(final):
+        q = p.copy()
+        q[final] = p[list(perm)]
+        if abs(O.me(proc, q[None])[0] / me0 - 1) < 1e-12:
+            count += 1
+    return count
+
+
+@pytest.mark.parametrize("n,seed", [(3, 61), (4, 62), (5, 63)])
+def test_spin_colour_summed_me_and_normalisation(n, seed):
+    """The per-event ME (paper Sect. 1: the LO |M|^2 averaged over initial
+    spins and colours) rebuilt outside mgo_me: every one of the 2^(n+2) spin
+    states in a helicity basis built here (circular gluon polarisations, top
+    helicity spinors), the colour sum by the colour-dressed recursion summed
+    over every colour assignment (n <= 4; for n = 5, A^dagger C A, which that
+    recursion pins at n <= 4), divided by 2*2 initial gluon polarisations,
+    8*8 initial gluon colours and the final-state symmetry factor counted from
+    Bose symmetry.  Catches a spin state dropped or counted twice and a wrong
+    identical-particle factor in the oracle's helicity loop."""
+    from concurrent.futures import ThreadPoolExecutor
+    proc = PROC_N[n]
+    par = O.Params()
+    p = process_momenta(proc, SQRTS[n], 1, seed)[0]
+    gam = O.gamma()
+    us = _helicity_spinors(p[2], par.mt)[0]
+    vs = _helicity_spinors(p[3], par.mt)[1]
+    for s in range(2):  # valid, complete spinors of the oracle's representation
+        ps_t, ps_tb = _slash(p[2]), _slash(p[3])
+        np.testing.assert_allclose((ps_t - par.mt * np.eye(4)) @ us[s], 0, atol=1e-10 * p[2, 0])
+        np.testing.assert_allclose((ps_tb + par.mt * np.eye(4)) @ vs[s], 0, atol=1e-10 * p[3, 0])
+    ubars = [u.conj() @ gam[0] for u in us]
+    np.testing.assert_allclose(sum(np.outer(us[s], ubars[s]) for s in range(2)),
+                               _slash(p[2]) + par.mt * np.eye(4), atol=1e-11 * p[2, 0])
+    slots = [0, 1] + list(range(4, n + 2))
+    kin = np.array([p[s] if s < 2 else -p[s] for s in slots])
+    pols = [_circular_polarisations(p[s], outgoing=s >= 2) for s in slots]
+    summed = O.dressed_colour_sum if n <= 4 else O.ordered_colour_sum
+
+    def one_state(h):
+        eps = np.array([pols[i][(h >> i) & 1] for i in range(n)])
+        st, stb = (h >> n) & 1, (h >> (n + 1)) & 1
+        return summed(n, kin, eps, p[2], ubars[st], p[3], vs[stb], par)
+
+    with ThreadPoolExecutor(8) as ex:
+        total = sum(ex.map(one_state, range(1 << (n + 2))))
+    sym = _final_gluon_symmetry(proc, p, n)
+    assert sym == math.factorial(n - 2)  # identical final gluons only
+    iden = 2 * 2 * O.generators().shape[0] ** 2 * sym
+    assert iden == {3: 256, 4: 512, 5: 1536}[n]  # the normalisation of the matrix element definition
+    assert abs(total / iden / O.me(proc, p[None])[0] - 1) < 1e-12
