@@ -104,7 +104,13 @@ int mg_process_info(const mg_process* h, int* npar, int* n_hel, int* n_col, int*
  * and keeps helicity h iff max over the events of |M_h|^2 / sum_h' |M_h'|^2
  * exceeds 1e-14.  Synchronous.  n_good_out (may be NULL) receives the count;
  * mask_host (may be NULL) receives n_hel bytes, 1 = kept.  nevt = 0 restores
- * all helicities.  Uses a temporary device buffer of nevt * n_hel doubles. */
+ * all helicities, and so does a calibration set in which no event has a
+ * positive finite |M|^2 (it carries no information about the helicities).
+ * Uses a temporary device buffer of nevt * n_hel doubles.  A list that differs
+ * from the handle's current one is stored in a new device array; the old one
+ * stays allocated until the handle is destroyed, since launches already queued
+ * or CUDA graphs the caller captured may still read it (n_hel ints per
+ * change). */
 int mg_good_helicities(mg_process* h, const double* momenta_dev, int64_t nevt, int* n_good_out,
                        uint8_t* mask_host);
 
@@ -116,6 +122,13 @@ int mg_good_helicities(mg_process* h, const double* momenta_dev, int64_t nevt, i
  * Errors: MG_ERR_ARG (NULL handle/pointer, nevt < 0, misaligned momenta),
  * MG_ERR_CUDA (launch failure, or no memory for that workspace). */
 int mg_sigma(mg_process* h, const double* momenta_dev, int64_t nevt, double* me_out_dev, void* stream);
+
+/* Device bytes that one mg_sigma call of nevt events takes from the
+ * stream-ordered allocator with the handle's current helicity list: the
+ * two-phase workspace of the mixed g g > t t~ g g g path, 0 for every other
+ * process and precision.  For memory planning (the serving loop's admission
+ * counts it).  Errors: MG_ERR_ARG (NULL, nevt < 0). */
+int mg_sigma_workspace_bytes(mg_process* h, int64_t nevt, int64_t* bytes_out);
 
 /* Same computation from host buffers: copies momenta_host to a handle-owned
  * device workspace, launches, copies the MEs back into me_out_host and waits
@@ -169,6 +182,10 @@ int mg_sigma_helicities(mg_process* h, const double* momenta_dev, int64_t nevt, 
  *     overlap on the GPU -- from several host threads, or with any other use
  *     of the array -- race; serialise them.  The call synchronises the device
  *     first, so no launch of this handle may be pending in another thread.
+ *   - The list is rewritten in place: a CUDA graph that the caller captured
+ *     with this handle before the call must be captured again.
+ *   - A calibration set in which no event has a positive finite |M|^2
+ *     restores all helicities, as in mg_good_helicities.
  *   - Synchronous; runs on the legacy default stream. */
 #define MG_STATIC_SCRATCH_DOUBLES (1 << 20)
 #define MG_STATIC_MAX_HEL 128
@@ -206,18 +223,23 @@ int mg_unweight(const double* w_dev, const double* r_dev, int64_t n, double w_ma
 /* ---------------------------------------------------------------------------
  * Serving: a persistent request loop on one GPU with continuous batching
  * (paper Sect. 2, Fig. 1: several host processes sharing one GPU).
- * Requests (process handle + batch of events) are admitted while the in-flight
- * device memory stays within mem_budget_bytes, padded up to a shape bucket
+ * Requests (process handle + batch of events) are padded up to a shape bucket
  * (powers of two from min_bucket to max_bucket events; larger requests are
- * split into max_bucket pieces), and replayed as captured CUDA graphs, one
- * graph per (process, bucket), on n_streams streams, so that requests that
- * arrive while others run overlap on the device.
+ * split into max_bucket pieces) and admitted while the in-flight device memory
+ * -- each piece's momenta and results plus the workspace its launch takes
+ * (mg_sigma_workspace_bytes: the two-phase mixed g g > t t~ g g g path) --
+ * stays within mem_budget_bytes; they run as captured CUDA graphs, one graph
+ * per (stream, process, bucket, helicity list), on n_streams streams, so that
+ * requests that arrive while others run overlap on the device.  Host buffers
+ * travel through pinned staging buffers owned by the server, so every copy is
+ * asynchronous and no copy or launch runs under the lock that submit and poll
+ * take.
  * ------------------------------------------------------------------------- */
 typedef struct mg_server mg_server;
 
 typedef struct {
   int n_streams;             /* concurrent device streams          (default 4)        */
-  int64_t mem_budget_bytes;  /* in-flight device memory cap     (default 1 GiB)       */
+  int64_t mem_budget_bytes;  /* in-flight device memory cap     (default 8 GiB)       */
   int64_t min_bucket;        /* smallest padded batch              (default 256)      */
   int64_t max_bucket;        /* largest padded batch               (default 65536)    */
   int use_graphs;            /* 1: per-bucket CUDA graphs, 0: plain launches (default 1) */
@@ -238,14 +260,15 @@ int mg_server_cfg_default(mg_server_cfg* cfg);
 /* Start the server (one host scheduler thread) on the current device. */
 int mg_server_create(const mg_server_cfg* cfg, mg_server** out);
 
-/* Queue a request: nevt events momenta[nevt][npar][4] (host memory), results
- * written to me_out[nevt] (host memory) before the request completes.  Both
+/* Queue a request: nevt events momenta[nevt][npar][4], results written to
+ * me_out[nevt] before the request completes.  Each buffer may be in host or
+ * in device memory (told apart with cudaPointerGetAttributes).  Both
  * buffers are the caller's and must stay valid until mg_server_poll has
  * returned MG_OK or an error for the request, and so must the process handle
  * h (it may be destroyed after that; the graphs the server captured for it
  * are keyed by the handle's own serial number and are not replayed for a
- * later handle).  Non-blocking.  A request larger than the memory budget can
- * never be admitted: MG_ERR_NOMEM at submit. */
+ * later handle).  Non-blocking.  A request whose pieces need more than the
+ * memory budget each can never be admitted: MG_ERR_NOMEM at submit. */
 int mg_server_submit(mg_server* s, mg_process* h, const double* momenta, int64_t nevt, double* me_out,
                      uint64_t* req_id);
 

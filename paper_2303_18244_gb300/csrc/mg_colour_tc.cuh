@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(NT, MG_TC_MINB) sigma_tc_kernel(const double* 
     if (tid == 0) colour_mma<K, N>(tmem, a_addr, b_addr, LY::a_tile, mma_bar);
     // the outcome of the bounded wait is made uniform across the CTA, so that
     // no thread can skip the warp-collective TMEM loads or a barrier alone
-    if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, WAIT_POLLS) ? 1 : 0)) {
+    if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, kp.polls) ? 1 : 0)) {
       if (tid == 0) atomicOr(status, ST_MMA_TIMEOUT);
       ok = false;
       break;
@@ -374,7 +374,7 @@ template <class P>
 __global__ void __launch_bounds__(128, 1)
     colour_rows_tc_kernel(const float2* __restrict__ J, long long ldj, long long nevt, double* __restrict__ me,
                           int nhel, int first, int last, const uint4* __restrict__ ctile,
-                          unsigned* __restrict__ status) {
+                          unsigned* __restrict__ status, uint32_t polls) {
   using LY = LayoutRows<P>;
   constexpr int NT = 128, K = LY::K, N = LY::N;
   static_assert(2 * N <= 256, "two accumulators of N columns");
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(128, 1)
       tc::mma_commit(mma_bar);
     }
     // bounded wait, outcome uniform across the CTA (see sigma_tc_kernel)
-    if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, WAIT_POLLS) ? 1 : 0)) {
+    if (!__syncthreads_and(mbar_wait_bounded(mma_bar, phase, polls) ? 1 : 0)) {
       if (tid == 0) atomicOr(status, ST_MMA_TIMEOUT);
       ok = false;
       break;
@@ -702,6 +702,20 @@ int launch_sigma_tmem64(const LaunchArgs& a) {
 // ROWS_WORKSPACE bytes of flows (FP32 complex [slice][NCOL][events]).
 constexpr size_t ROWS_WORKSPACE = size_t(1) << 30;
 
+// Rows per event padded to 128, and the helicities of one slice: as many as
+// fit ROWS_WORKSPACE (at least one, at most nhel).
+inline long long rows_ld(long long nevt) { return (nevt + 127) / 128 * 128; }
+inline long long rows_slice(int ncol, long long nevt, int nhel) {
+  const size_t per_hel = (size_t)ncol * (size_t)rows_ld(nevt) * sizeof(float2);
+  const long long hs = (long long)(ROWS_WORKSPACE / per_hel);
+  return hs < 1 ? 1 : (hs > nhel ? nhel : hs);
+}
+// bytes one two-phase launch takes from the stream-ordered allocator
+inline size_t rows_workspace_bytes(int ncol, long long nevt, int nhel) {
+  if (nevt <= 0 || nhel <= 0) return 0;
+  return (size_t)rows_slice(ncol, nevt, nhel) * (size_t)ncol * (size_t)rows_ld(nevt) * sizeof(float2);
+}
+
 template <class P, int NT>
 int launch_sigma_rows(const LaunchArgs& a) {
   static_assert(128 % NT == 0, "flow rows are padded to 128 events");
@@ -718,12 +732,13 @@ int launch_sigma_rows(const LaunchArgs& a) {
   static const cudaError_t attr2 = set_smem_attr(colour_rows_tc_kernel<P>, smem2);
   if (attr1 != cudaSuccess || attr2 != cudaSuccess) return -4;
   if (a.nevt <= 0 || a.nhel <= 0) return 0;
-  const long long ldj = (a.nevt + 127) / 128 * 128;
-  const size_t per_hel = (size_t)P::NCOL * (size_t)ldj * sizeof(float2);
-  long long hs = (long long)(ROWS_WORKSPACE / per_hel);
-  hs = hs < 1 ? 1 : (hs > a.nhel ? a.nhel : hs);
+  const long long ldj = rows_ld(a.nevt);
+  const long long hs = rows_slice(P::NCOL, a.nevt, a.nhel);
   float2* J = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&J), (size_t)hs * per_hel, a.stream) != cudaSuccess) return -4;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&J), rows_workspace_bytes(P::NCOL, a.nevt, a.nhel), a.stream) !=
+      cudaSuccess)
+    return -4;
+  if (a.marks) a.marks->mark(a.stream);
   for (int h0 = 0; h0 < a.nhel; h0 += (int)hs) {
     const int nh = a.nhel - h0 < hs ? a.nhel - h0 : (int)hs;
     if constexpr (tmem_flows)
@@ -732,8 +747,11 @@ int launch_sigma_rows(const LaunchArgs& a) {
     else
       flows_kernel<P, NT><<<(unsigned)((a.nevt + NT - 1) / NT), NT, smem1, a.stream>>>(
           a.mom, a.nevt, J, ldj, a.hels + h0, nh, a.kp, a.status);
+    if (a.marks) a.marks->mark(a.stream);
     colour_rows_tc_kernel<P><<<(unsigned)(ldj / 128), 128, smem2, a.stream>>>(
-        J, ldj, a.nevt, a.out, nh, h0 == 0, h0 + nh == a.nhel, static_cast<const uint4*>(a.ctile), a.status);
+        J, ldj, a.nevt, a.out, nh, h0 == 0, h0 + nh == a.nhel, static_cast<const uint4*>(a.ctile), a.status,
+        a.kp.polls);
+    if (a.marks) a.marks->mark(a.stream);
   }
   const cudaError_t e1 = cudaGetLastError();
   const cudaError_t e2 = cudaFreeAsync(J, a.stream);

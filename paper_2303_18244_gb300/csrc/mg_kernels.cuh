@@ -26,6 +26,7 @@ namespace mg {
 
 struct KParams {
   double v[8];
+  uint32_t polls;  // bound of the first wait on each device barrier (the drain after a timeout uses WAIT_POLLS)
 };
 
 // status bits written by kernels
@@ -127,9 +128,10 @@ __device__ __forceinline__ int load_and_prepare_at(uint64_t* bar, double* stage,
   }
   __syncthreads();
   // the outcome of the bounded wait is made uniform across the CTA
-  if (!__syncthreads_and(mbar_wait_bounded(bar, 0, WAIT_POLLS) ? 1 : 0)) {
-    // the copy did not complete: flag it, wait once more (bounded) so that no
-    // copy is left in flight into this CTA's shared memory, and give up
+  if (!__syncthreads_and(mbar_wait_bounded(bar, 0, kp.polls) ? 1 : 0)) {
+    // the copy did not complete: flag it, wait once more (bounded, full
+    // length) so that no copy is left in flight into this CTA's shared
+    // memory, and give up
     if (tid == 0) atomicOr(status, ST_TMA_TIMEOUT);
     mbar_wait_bounded(bar, 0, WAIT_POLLS);
     return -1;
@@ -350,6 +352,18 @@ struct LaunchArgs {
   int* hel_out;
   int* col_out;
   double* colw_out;
+  // diagnostics (may be null): events recorded on the stream before the first
+  // and after every kernel of a multi-kernel launch
+  struct PhaseMarks* marks;
+};
+
+struct PhaseMarks {
+  static constexpr int MAX = 257;
+  cudaEvent_t ev[MAX];
+  int n = 0;
+  void mark(cudaStream_t s) {
+    if (n < MAX) cudaEventRecord(ev[n++], s);
+  }
 };
 
 template <class K>
@@ -420,6 +434,7 @@ struct ProcDesc {
   int (*select_mixed)(const LaunchArgs&);
   int (*sigma_paper)(const LaunchArgs&);
   int (*sigma_float)(const LaunchArgs&);  // all-float mode
+  int rows_mixed;  // 1: the mixed path runs in two phases through a stream-ordered HBM workspace
 };
 
 }  // namespace mg

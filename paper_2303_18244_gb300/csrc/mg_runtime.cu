@@ -2,6 +2,7 @@
 // filter, per-event ME launches from device or host buffers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -66,6 +67,7 @@ extern "C" int mg_params_default(mg_params* p) {
 // Couplings per process (standard model, G_F scheme for the electroweak sector).
 static int make_kparams(const ProcDesc* d, const mg_params& p, KParams& kp) {
   std::memset(&kp, 0, sizeof(kp));
+  kp.polls = mg::WAIT_POLLS;
   if (std::strcmp(d->tag, "eemumu") == 0) {
     if (!(p.alpha_em_inv > 0) || !(p.mz > 0) || !(p.wz >= 0) || !(p.gf > 0)) return MG_ERR_ARG;
     const double pi = 3.14159265358979323846;
@@ -198,17 +200,15 @@ extern "C" int mg_process_info(const mg_process* h, int* npar, int* n_hel, int* 
   return MG_OK;
 }
 
-int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, cudaStream_t stream) {
+int mg_launch_sigma_locked(mg_process* h, const double* mom, int64_t nevt, double* me, cudaStream_t stream,
+                           mg::PhaseMarks* marks) {
   LaunchArgs a{};
+  a.marks = marks;
   a.mom = mom;
   a.nevt = nevt;
   a.out = me;
-  {
-    // the list and its length together (mg_good_helicities may replace them)
-    std::lock_guard<std::mutex> lk(h->lock);
-    a.hels = h->d_hels;
-    a.nhel = h->n_good;
-  }
+  a.hels = h->d_hels;
+  a.nhel = h->n_good;
   a.kp = h->kp;
   a.ctile = h->d_ctile;
   a.status = h->d_status;
@@ -218,6 +218,24 @@ int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, 
                  : h->par.precision == MG_FLOAT       ? h->d->sigma_float(a)
                                                       : h->d->sigma_fp64(a);
   return rc ? MG_ERR_CUDA : MG_OK;
+}
+
+int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, cudaStream_t stream) {
+  // the list and its length together (mg_good_helicities may replace them)
+  std::lock_guard<std::mutex> lk(h->lock);
+  return mg_launch_sigma_locked(h, mom, nevt, me, stream);
+}
+
+int64_t mg_workspace_bytes_locked(const mg_process* h, int64_t nevt) {
+  if (h->par.precision != MG_MIXED || !h->d->rows_mixed) return 0;
+  return (int64_t)mg::rows_workspace_bytes(h->d->ncol, nevt, h->n_good);
+}
+
+extern "C" int mg_sigma_workspace_bytes(mg_process* h, int64_t nevt, int64_t* bytes_out) {
+  if (!h || nevt < 0 || !bytes_out) return MG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->lock);
+  *bytes_out = mg_workspace_bytes_locked(h, nevt);
+  return MG_OK;
 }
 
 extern "C" int mg_sigma(mg_process* h, const double* momenta_dev, int64_t nevt, double* me_out_dev, void* stream) {
@@ -240,11 +258,6 @@ extern "C" int mg_sigma_select(mg_process* h, const double* momenta_dev, int64_t
   a.mom = momenta_dev;
   a.nevt = nevt;
   a.out = me_out_dev;
-  {
-    std::lock_guard<std::mutex> lk(h->lock);
-    a.hels = h->d_hels;
-    a.nhel = h->n_good;
-  }
   a.kp = h->kp;
   a.status = h->d_status;
   a.stream = static_cast<cudaStream_t>(stream);
@@ -252,6 +265,10 @@ extern "C" int mg_sigma_select(mg_process* h, const double* momenta_dev, int64_t
   a.hel_out = hel_out_dev;
   a.col_out = col_out_dev;
   a.colw_out = colw_out_dev;
+  // the list and its length together, up to the launch
+  std::lock_guard<std::mutex> lk(h->lock);
+  a.hels = h->d_hels;
+  a.nhel = h->n_good;
   // the paper-style mode chooses from its FP64 amplitudes
   const bool fp32 = h->par.precision == MG_MIXED || h->par.precision == MG_FLOAT;
   const int rc = fp32 ? h->d->select_mixed(a) : h->d->select_fp64(a);
@@ -331,12 +348,25 @@ extern "C" int mg_good_helicities(mg_process* h, const double* momenta_dev, int6
         if (r > maxr[k]) maxr[k] = r;
       }
     }
-    for (int k = 0; k < nhel; k++) mask[k] = maxr[k] > 1e-14 ? 1 : 0;
+    bool any = false;
+    for (int k = 0; k < nhel; k++) {
+      mask[k] = maxr[k] > 1e-14 ? 1 : 0;
+      any |= mask[k] != 0;
+    }
+    // no event with a positive finite |M|^2: the set says nothing, keep all
+    if (!any) std::fill(mask.begin(), mask.end(), 1);
   }
   std::vector<int> good;
   for (int k = 0; k < nhel; k++)
     if (mask[k]) good.push_back(k);
-  if (good.empty()) good.push_back(0);  // keep the launch well-formed; ME is then 0
+  {
+    std::lock_guard<std::mutex> lk(h->lock);
+    if (mask == h->mask) {  // unchanged: keep the list, its version and its graphs
+      if (n_good_out) *n_good_out = h->n_good;
+      if (mask_host) std::memcpy(mask_host, mask.data(), nhel);
+      return MG_OK;
+    }
+  }
   int* nd = nullptr;
   if (cudaMalloc(&nd, sizeof(int) * nhel) != cudaSuccess) return MG_ERR_NOMEM;
   if (cudaMemcpy(nd, good.data(), sizeof(int) * good.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -345,14 +375,15 @@ extern "C" int mg_good_helicities(mg_process* h, const double* momenta_dev, int6
   }
   {
     std::lock_guard<std::mutex> lk(h->lock);
-    // launches already queued may still read the previous list: keep it alive
+    // launches already queued, and graphs the caller captured, may still read
+    // the previous list: keep it alive until the handle is destroyed
     h->old_hels.push_back(h->d_hels);
     h->d_hels = nd;
     h->n_good = (int)good.size();
     h->mask = mask;
     h->hel_version++;
   }
-  if (n_good_out) *n_good_out = h->n_good;
+  if (n_good_out) *n_good_out = (int)good.size();
   if (mask_host) std::memcpy(mask_host, mask.data(), nhel);
   return MG_OK;
 }

@@ -16,7 +16,8 @@ struct mg_process {
   mg::KParams kp{};
   int device = 0;
   int* d_hels = nullptr;            // good helicity indices [n_good] (device)
-  std::vector<int*> old_hels;       // superseded lists, freed at destroy
+  std::vector<int*> old_hels;       // superseded lists (queued launches and captured graphs may
+                                    // still read them), freed at destroy
   int n_good = 0;
   unsigned hel_version = 0;         // bumped when the helicity list changes
   std::vector<uint8_t> mask;
@@ -30,5 +31,12 @@ struct mg_process {
   int64_t cap = 0;
 };
 
-// stream-ordered launch of the handle's sigma kernel (no argument checks)
+// stream-ordered launch of the handle's sigma kernel (no argument checks);
+// takes h->lock, so that the helicity list and its length are read together
 int mg_launch_sigma(mg_process* h, const double* mom, int64_t nevt, double* me, cudaStream_t stream);
+// the same with h->lock already held by the caller; marks (may be null)
+// records an event before and after each kernel of a multi-kernel launch
+int mg_launch_sigma_locked(mg_process* h, const double* mom, int64_t nevt, double* me, cudaStream_t stream,
+                           mg::PhaseMarks* marks = nullptr);
+// stream-ordered workspace bytes of one launch of nevt events (h->lock held)
+int64_t mg_workspace_bytes_locked(const mg_process* h, int64_t nevt);

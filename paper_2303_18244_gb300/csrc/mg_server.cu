@@ -3,22 +3,31 @@
 // The paper (Sect. 2, Fig. 1) runs several host processes against one GPU and
 // finds that their matrix-element launches interleave and raise the combined
 // throughput.  Here one scheduler thread plays that role for many clients:
-//   - requests (process handle, host momenta, event count) wait in a FIFO;
+//   - requests (process handle, momenta in host or device memory, event
+//     count) wait in a FIFO;
 //   - a request is split into chunks of at most max_bucket events; each chunk
 //     is padded up to a power-of-two shape bucket (padding repeats the chunk's
 //     first event; padded results are discarded);
 //   - a chunk is admitted to one of n_streams device slots when a slot is free
-//     and the in-flight device bytes stay within mem_budget_bytes;
-//   - per slot: H2D copy, padding kernel, the sigma launch replayed from a
-//     CUDA graph captured once per (slot, process handle, bucket, helicity
-//     list) -- the handle by its serial number, never reused, so a graph is
-//     never replayed for a later handle that reuses a destroyed one's address,
-//     D2H copy, completion event -- so chunks that arrive while others run
-//     overlap on the device;
+//     and the in-flight device bytes -- the chunk's momenta and results plus
+//     the stream-ordered workspace its launch takes (the two-phase
+//     g g > t t~ g g g mixed path) -- stay within mem_budget_bytes (a chunk
+//     larger than the budget on its own runs when nothing else is in flight);
+//   - per slot: host momenta are copied into the slot's pinned staging buffer
+//     and sent with an asynchronous copy (device momenta: a device copy), the
+//     padding kernel runs, the sigma launch is replayed from a CUDA graph
+//     captured once per (slot, process handle, bucket, helicity list) -- the
+//     handle by its serial number, never reused, so a graph is never replayed
+//     for a later handle that reuses a destroyed one's address -- and the
+//     results go back through pinned staging; a completion event closes it;
+//   - the scheduler holds the server mutex only for queue and request
+//     bookkeeping: host copies, launches and graph captures run outside it, so
+//     submit and poll never wait for them, and every device copy is
+//     asynchronous, so chunks on different slots overlap on the device;
 //   - completions are observed by polling the slots' events; a request is done
 //     when its last chunk is.
 // The process constants, helicity lists and colour data stay resident in the
-// process handles; the slot buffers are allocated once at server creation.
+// process handles; slot buffers and staging are allocated at server creation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,6 +62,7 @@ struct Request {
   mg_process* h = nullptr;
   const double* mom = nullptr;
   double* me = nullptr;
+  bool mom_dev = false, me_dev = false;  // buffers in device memory
   int64_t nevt = 0;
   int64_t padded = 0;
   int chunks_left = 0;
@@ -71,6 +81,8 @@ struct Slot {
   cudaEvent_t done = nullptr;
   double* d_mom = nullptr;
   double* d_me = nullptr;
+  double* h_mom = nullptr;  // pinned staging of host momenta
+  double* h_me = nullptr;   // pinned staging of host results
   bool busy = false;
   Chunk cur{};
   int64_t bytes = 0;
@@ -78,26 +90,37 @@ struct Slot {
 
 constexpr int MAX_NPAR = 7;
 
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // unregistered host memory on older runtimes: clear the error
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 struct mg_server {
   mg_server_cfg cfg{};
   int device = 0;
-  std::vector<Slot> slots;
+  std::vector<Slot> slots;  // touched by the scheduler thread only
+  std::map<std::tuple<int, uint64_t, int64_t, unsigned>, cudaGraphExec_t> graphs;  // scheduler thread only
+  int64_t inflight = 0;                                                            // scheduler thread only
+  // shared with submit/poll, under m
+  std::mutex m;
   std::deque<Chunk> queue;
   std::unordered_map<uint64_t, Request*> reqs;
-  std::map<std::tuple<int, uint64_t, int64_t, unsigned>, cudaGraphExec_t> graphs;
-  std::mutex m;
   std::condition_variable cv_work, cv_done;
-  std::thread th;
   bool stop = false;
   uint64_t next_id = 1;
-  int64_t inflight = 0;
+  std::thread th;
   Clock::time_point t0 = Clock::now();
 
   double now_us() const { return std::chrono::duration<double, std::micro>(Clock::now() - t0).count(); }
   void run();
   int admit(int si, const Chunk& c);
+  void finish_chunk(Request* r, int rc);  // under m
 };
 
 static int64_t bucket_for(const mg_server_cfg& c, int64_t n) {
@@ -106,35 +129,59 @@ static int64_t bucket_for(const mg_server_cfg& c, int64_t n) {
   return std::min(b, c.max_bucket);
 }
 
-static int64_t chunk_bytes(const Chunk& c) { return c.bucket * (c.req->h->d->npar * 32 + 8); }
+// device bytes a chunk holds while in flight: momenta and results of its
+// bucket, and the workspace of its launch
+static int64_t chunk_bytes(mg_process* h, int64_t bucket) {
+  int64_t ws;
+  {
+    std::lock_guard<std::mutex> lk(h->lock);
+    ws = mg_workspace_bytes_locked(h, bucket);
+  }
+  return bucket * (h->d->npar * 32 + 8) + ws;
+}
 
+void mg_server::finish_chunk(Request* r, int rc) {
+  if (rc != MG_OK && r->status == MG_PENDING) r->status = rc;
+  if (--r->chunks_left == 0) {
+    if (r->status == MG_PENDING) r->status = MG_OK;
+    r->done = true;
+    r->done_us = now_us();
+    cv_done.notify_all();
+  }
+}
+
+// Runs on the scheduler thread without the server mutex.
 int mg_server::admit(int si, const Chunk& c) {
   Slot& s = slots[si];
   mg_process* h = c.req->h;
   const int row = h->d->npar * 4;
-  if (cudaMemcpyAsync(s.d_mom, c.req->mom + c.off * row, sizeof(double) * c.n * row, cudaMemcpyHostToDevice,
-                      s.stream) != cudaSuccess)
-    return MG_ERR_CUDA;
+  const size_t in_bytes = sizeof(double) * c.n * row;
+  const double* src = c.req->mom + c.off * row;
+  if (c.req->mom_dev) {
+    if (cudaMemcpyAsync(s.d_mom, src, in_bytes, cudaMemcpyDeviceToDevice, s.stream) != cudaSuccess)
+      return MG_ERR_CUDA;
+  } else {
+    std::memcpy(s.h_mom, src, in_bytes);  // the slot is idle: its staging is free
+    if (cudaMemcpyAsync(s.d_mom, s.h_mom, in_bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
+      return MG_ERR_CUDA;
+  }
   if (c.bucket > c.n) {
     const long long total = (c.bucket - c.n) * row;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 1024);
     pad_events<<<blocks, 256, 0, s.stream>>>(s.d_mom, row, c.n, c.bucket);
     if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
   }
-  int rc = MG_OK;
   if (cfg.use_graphs) {
-    unsigned ver;
-    {
-      std::lock_guard<std::mutex> lk(h->lock);
-      ver = h->hel_version;
-    }
-    auto key = std::make_tuple(si, h->serial, c.bucket, ver);
+    // the handle's lock from the helicity-list version to the launch: the
+    // graph and the list it reads belong together
+    std::lock_guard<std::mutex> lk(h->lock);
+    auto key = std::make_tuple(si, h->serial, c.bucket, h->hel_version);
     auto it = graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it == graphs.end()) {
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MG_ERR_CUDA;
-      rc = mg_launch_sigma(h, s.d_mom, c.bucket, s.d_me, s.stream);
+      const int rc = mg_launch_sigma_locked(h, s.d_mom, c.bucket, s.d_me, s.stream);
       const cudaError_t e = cudaStreamEndCapture(s.stream, &g);
       if (rc || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -149,59 +196,60 @@ int mg_server::admit(int si, const Chunk& c) {
     }
     if (cudaGraphLaunch(exec, s.stream) != cudaSuccess) return MG_ERR_CUDA;
   } else {
-    rc = mg_launch_sigma(h, s.d_mom, c.bucket, s.d_me, s.stream);
+    const int rc = mg_launch_sigma(h, s.d_mom, c.bucket, s.d_me, s.stream);
     if (rc) return rc;
   }
-  if (cudaMemcpyAsync(c.req->me + c.off, s.d_me, sizeof(double) * c.n, cudaMemcpyDeviceToHost, s.stream) !=
-      cudaSuccess)
+  const size_t out_bytes = sizeof(double) * c.n;
+  if (c.req->me_dev) {
+    if (cudaMemcpyAsync(c.req->me + c.off, s.d_me, out_bytes, cudaMemcpyDeviceToDevice, s.stream) != cudaSuccess)
+      return MG_ERR_CUDA;
+  } else if (cudaMemcpyAsync(s.h_me, s.d_me, out_bytes, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess) {
     return MG_ERR_CUDA;
+  }
   if (cudaEventRecord(s.done, s.stream) != cudaSuccess) return MG_ERR_CUDA;
   return MG_OK;
 }
 
 void mg_server::run() {
   cudaSetDevice(device);
-  std::unique_lock<std::mutex> lk(m);
   for (;;) {
     bool progress = false;
-    // completions
+    // completions (the slots belong to this thread; results leave the pinned
+    // staging before the request is marked done)
     for (Slot& s : slots) {
       if (!s.busy) continue;
       const cudaError_t q = cudaEventQuery(s.done);
       if (q == cudaErrorNotReady) continue;
       Request* r = s.cur.req;
-      if (q != cudaSuccess) r->status = MG_ERR_CUDA;
-      if (--r->chunks_left == 0) {
-        if (r->status == MG_PENDING) r->status = MG_OK;
-        r->done = true;
-        r->done_us = now_us();
-        cv_done.notify_all();
-      }
+      if (q == cudaSuccess && !r->me_dev) std::memcpy(r->me + s.cur.off, s.h_me, sizeof(double) * s.cur.n);
       s.busy = false;
       inflight -= s.bytes;
       progress = true;
+      std::lock_guard<std::mutex> lk(m);
+      finish_chunk(r, q == cudaSuccess ? MG_OK : MG_ERR_CUDA);
     }
-    if (stop) {
-      // fail everything still queued, then drain the slots
-      while (!queue.empty()) {
-        Request* r = queue.front().req;
-        queue.pop_front();
-        if (r->status == MG_PENDING) r->status = MG_ERR_STATE;
-        if (--r->chunks_left == 0) {
-          r->done = true;
-          r->done_us = now_us();
+    bool stopping;
+    {
+      std::lock_guard<std::mutex> lk(m);
+      stopping = stop;
+      if (stopping) {
+        // fail everything still queued, then drain the slots
+        while (!queue.empty()) {
+          Request* r = queue.front().req;
+          queue.pop_front();
+          finish_chunk(r, MG_ERR_STATE);
         }
+        cv_done.notify_all();
       }
-      cv_done.notify_all();
+    }
+    if (stopping) {
       bool any = false;
       for (Slot& s : slots) any |= s.busy;
       if (!any) break;
     }
-    // admissions, FIFO
-    while (!queue.empty()) {
-      const Chunk c = queue.front();
-      const int64_t need = chunk_bytes(c);
-      if (inflight + need > cfg.mem_budget_bytes) break;
+    // admissions, FIFO: the chunk is taken off the queue under the mutex, its
+    // copies and launches run without it
+    for (;;) {
       int si = -1;
       for (int i = 0; i < (int)slots.size(); i++)
         if (!slots[i].busy) {
@@ -209,34 +257,44 @@ void mg_server::run() {
           break;
         }
       if (si < 0) break;
-      queue.pop_front();
-      if (c.req->start_us < 0) c.req->start_us = now_us();
+      Chunk c;
+      {
+        std::lock_guard<std::mutex> lk(m);
+        if (queue.empty()) break;
+        c = queue.front();
+      }
+      const int64_t need = chunk_bytes(c.req->h, c.bucket);
+      if (inflight > 0 && inflight + need > cfg.mem_budget_bytes) break;
+      {
+        std::lock_guard<std::mutex> lk(m);
+        queue.pop_front();  // only this thread pops: still the chunk read above
+        if (c.req->start_us < 0) c.req->start_us = now_us();
+      }
       const int rc = admit(si, c);
+      progress = true;
       if (rc != MG_OK) {
-        c.req->status = rc;
         // the slot's stream may hold part of the chunk's work: wait for it
         cudaStreamSynchronize(slots[si].stream);
-        if (--c.req->chunks_left == 0) {
-          c.req->done = true;
-          c.req->done_us = now_us();
-          cv_done.notify_all();
-        }
-      } else {
-        slots[si].busy = true;
-        slots[si].cur = c;
-        slots[si].bytes = need;
-        inflight += need;
+        std::lock_guard<std::mutex> lk(m);
+        finish_chunk(c.req, rc);
+        continue;
       }
-      progress = true;
+      slots[si].busy = true;
+      slots[si].cur = c;
+      slots[si].bytes = need;
+      inflight += need;
     }
-    if (!progress) cv_work.wait_for(lk, std::chrono::microseconds(20));
+    if (!progress) {
+      std::unique_lock<std::mutex> lk(m);
+      cv_work.wait_for(lk, std::chrono::microseconds(20));
+    }
   }
 }
 
 extern "C" int mg_server_cfg_default(mg_server_cfg* cfg) {
   if (!cfg) return MG_ERR_ARG;
   cfg->n_streams = 4;
-  cfg->mem_budget_bytes = int64_t(1) << 30;
+  cfg->mem_budget_bytes = int64_t(8) << 30;
   cfg->min_bucket = 256;
   cfg->max_bucket = 65536;
   cfg->use_graphs = 1;
@@ -264,11 +322,12 @@ extern "C" int mg_server_create(const mg_server_cfg* cfg, mg_server** out) {
     return MG_ERR_CUDA;
   }
   s->slots.resize(c.n_streams);
+  const size_t mom_bytes = sizeof(double) * c.max_bucket * MAX_NPAR * 4, me_bytes = sizeof(double) * c.max_bucket;
   for (Slot& sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc(&sl.d_mom, sizeof(double) * c.max_bucket * MAX_NPAR * 4) != cudaSuccess ||
-        cudaMalloc(&sl.d_me, sizeof(double) * c.max_bucket) != cudaSuccess) {
+        cudaMalloc(&sl.d_mom, mom_bytes) != cudaSuccess || cudaMalloc(&sl.d_me, me_bytes) != cudaSuccess ||
+        cudaMallocHost(&sl.h_mom, mom_bytes) != cudaSuccess || cudaMallocHost(&sl.h_me, me_bytes) != cudaSuccess) {
       s->stop = true;
       mg_server_destroy(s);
       return MG_ERR_NOMEM;
@@ -289,11 +348,15 @@ extern "C" int mg_server_submit(mg_server* s, mg_process* h, const double* momen
   r->mom = momenta;
   r->me = me_out;
   r->nevt = nevt;
+  if (nevt > 0) {
+    r->mom_dev = is_device_pointer(momenta);
+    r->me_dev = is_device_pointer(me_out);
+  }
   std::vector<Chunk> cs;
   for (int64_t off = 0; off < nevt; off += s->cfg.max_bucket) {
     const int64_t n = std::min(s->cfg.max_bucket, nevt - off);
     Chunk c{r, off, n, bucket_for(s->cfg, n)};
-    if (chunk_bytes(c) > s->cfg.mem_budget_bytes) {
+    if (chunk_bytes(h, c.bucket) > s->cfg.mem_budget_bytes) {
       delete r;
       return MG_ERR_NOMEM;  // could never be admitted
     }
@@ -362,6 +425,8 @@ extern "C" void mg_server_destroy(mg_server* s) {
     if (sl.stream) cudaStreamDestroy(sl.stream);
     cudaFree(sl.d_mom);
     cudaFree(sl.d_me);
+    cudaFreeHost(sl.h_mom);
+    cudaFreeHost(sl.h_me);
   }
   for (auto& kv : s->reqs) delete kv.second;
   if (prev >= 0) cudaSetDevice(prev);

@@ -105,21 +105,26 @@ extern "C" int mg_good_helicities_static(mg_process* h, const double* momenta_de
       cudaMemset(h->d_status, 0, sizeof(unsigned));
       return MG_ERR_TIMEOUT;
     }
+    bool any = false;
     for (int k = 0; k < nhel; k++) {
       double r;
       std::memcpy(&r, &res[k], sizeof(r));
       mask[k] = r > 1e-14 ? 1 : 0;
+      any |= mask[k] != 0;
     }
+    // no event with a positive finite |M|^2: the set says nothing, keep all
+    if (!any)
+      for (int k = 0; k < nhel; k++) mask[k] = 1;
   }
   int good[MG_STATIC_MAX_HEL];
   int n = 0;
   for (int k = 0; k < nhel; k++)
     if (mask[k]) good[n++] = k;
-  if (n == 0) good[n++] = 0;  // keep the launch well-formed; the ME is then 0
-  // the handle's list has room for every helicity: overwrite it in place
-  if (cudaMemcpy(h->d_hels, good, sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess) return MG_ERR_CUDA;
   {
+    // the handle's list has room for every helicity: overwrite it in place,
+    // under the lock, so that the list and its length change together
     std::lock_guard<std::mutex> lk(h->lock);
+    if (cudaMemcpy(h->d_hels, good, sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess) return MG_ERR_CUDA;
     h->n_good = n;
     std::copy(mask, mask + nhel, h->mask.begin());
     h->hel_version++;

@@ -28,12 +28,13 @@ MG_PHOTON_ONLY = 2
 # every symbol declared in include/mg.h
 EXPORTS = (
     "mg_params_default", "mg_process_create", "mg_process_destroy", "mg_process_info",
-    "mg_good_helicities", "mg_sigma", "mg_sigma_host", "mg_process_status", "mg_sigma_helicities",
+    "mg_good_helicities", "mg_sigma", "mg_sigma_workspace_bytes", "mg_sigma_host", "mg_process_status",
+    "mg_sigma_helicities",
     "mg_good_helicities_static", "mg_rambo", "mg_sigma_select", "mg_unweight",
     "mg_server_cfg_default", "mg_server_create", "mg_server_submit", "mg_server_poll",
     "mg_server_destroy", "mg_strerror",
     # include/mg_diag.h
-    "mg_diag_fma_peak",
+    "mg_diag_fma_peak", "mg_diag_sigma_phases", "mg_diag_set_wait_polls",
 )
 
 
@@ -81,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.mg_good_helicities.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
         L.mg_good_helicities_static.argtypes = [vp, vp, i64, ip, ctypes.POINTER(ctypes.c_uint8)]
         L.mg_sigma.argtypes = [vp, vp, i64, vp, vp]
+        L.mg_sigma_workspace_bytes.argtypes = [vp, i64, ctypes.POINTER(i64)]
         L.mg_rambo.argtypes = [vp, ctypes.c_double, ctypes.c_uint64, i64, i64, vp, vp]
         L.mg_unweight.argtypes = [vp, vp, i64, ctypes.c_double, vp, vp, vp]
         L.mg_sigma_select.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
@@ -94,6 +96,9 @@ def lib() -> ctypes.CDLL:
         L.mg_server_destroy.argtypes = [vp]
         L.mg_server_destroy.restype = None
         L.mg_diag_fma_peak.argtypes = [ctypes.c_int, dp]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.mg_diag_sigma_phases.argtypes = [vp, vp, i64, vp, vp, fp, fp, ip]
+        L.mg_diag_set_wait_polls.argtypes = [vp, ctypes.c_uint32]
         L.mg_strerror.argtypes = [ctypes.c_int]
         L.mg_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -211,6 +216,13 @@ def sigma(h: Process, momenta_dev, me_out_dev, stream=None, nevt: int | None = N
            "mg_sigma")
 
 
+def sigma_workspace_bytes(h: Process, nevt: int) -> int:
+    """mg_sigma_workspace_bytes: stream-ordered device bytes one mg_sigma call of nevt events takes."""
+    b = ctypes.c_int64()
+    _check(lib().mg_sigma_workspace_bytes(h.handle, nevt, ctypes.byref(b)), "mg_sigma_workspace_bytes")
+    return b.value
+
+
 def rambo(h: Process, sqrt_s: float, seed: int, first_event: int, momenta_dev, stream=None):
     """mg_rambo: fill momenta_dev[nevt][npar][4] with device-generated phase space."""
     nevt = momenta_dev.shape[0]
@@ -276,6 +288,12 @@ def _host_ptr(a) -> int:
     raise TypeError("expected a contiguous float64 host array")
 
 
+def _any_ptr(a) -> int:
+    if isinstance(a, np.ndarray):
+        return _host_ptr(a)
+    return _dev_check(a) if getattr(a, "is_cuda", False) else _host_ptr(a)
+
+
 class Server:
     """Owning wrapper of an mg_server (continuous-batching request loop)."""
 
@@ -289,10 +307,12 @@ class Server:
         _check(lib().mg_server_create(ctypes.byref(c), ctypes.byref(s)), "mg_server_create")
         self.handle = s
 
-    def submit(self, h: Process, momenta_host, me_out_host) -> int:
+    def submit(self, h: Process, momenta, me_out) -> int:
+        """Queue a request; momenta and me_out are host arrays (numpy or CPU
+        tensors) or float64 CUDA tensors, each on its own."""
         rid = ctypes.c_uint64()
-        _check(lib().mg_server_submit(self.handle, h.handle, _host_ptr(momenta_host), momenta_host.shape[0],
-                                      _host_ptr(me_out_host), ctypes.byref(rid)), "mg_server_submit")
+        _check(lib().mg_server_submit(self.handle, h.handle, _any_ptr(momenta), momenta.shape[0],
+                                      _any_ptr(me_out), ctypes.byref(rid)), "mg_server_submit")
         return rid.value
 
     def poll(self, req_id: int, timeout_us: int = 0):
@@ -319,3 +339,21 @@ def diag_fma_peak(kind: int) -> float:
     g = ctypes.c_double()
     _check(lib().mg_diag_fma_peak(kind, ctypes.byref(g)), "mg_diag_fma_peak")
     return g.value
+
+
+def diag_sigma_phases(h: Process, momenta_dev, me_out_dev, stream=None):
+    """(ms of the first kernels, ms of the second kernels, slices) of one
+    two-phase mg_sigma call, timed kernel by kernel (include/mg_diag.h)."""
+    a, b, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
+    _check(lib().mg_diag_sigma_phases(h.handle, _dev_check(momenta_dev), momenta_dev.shape[0], _dev_check(me_out_dev),
+                                      _stream_ptr(stream), ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+           "mg_diag_sigma_phases")
+    return a.value, b.value, n.value
+
+
+DIAG_WAIT_POLLS = 1 << 22
+
+
+def diag_set_wait_polls(h: Process, polls: int):
+    """Bound of the first wait on each device barrier of h's kernels (include/mg_diag.h)."""
+    _check(lib().mg_diag_set_wait_polls(h.handle, polls), "mg_diag_set_wait_polls")
