@@ -1,8 +1,12 @@
-// mg_diag.cu -- FMA peak probe (include/mg_diag.h).
+// mg_diag.cu -- FMA peak probe and per-kernel timing of a two-phase ME call
+// (include/mg_diag.h).
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "mg.h"
 #include "mg_diag.h"
+#include "mg_runtime_internal.h"
 
 namespace {
 
@@ -61,4 +65,56 @@ extern "C" int mg_diag_fma_peak(int kind, double* gflops) {
   if (kind == MG_DIAG_FP32) return run<float>(gflops);
   if (kind == MG_DIAG_FP64) return run<double>(gflops);
   return MG_ERR_ARG;
+}
+
+extern "C" int mg_diag_sigma_phases(mg_process* h, const double* momenta_dev, int64_t nevt, double* me_out_dev,
+                                    void* stream, float* ms_first, float* ms_second, int* slices) {
+  if (!h || nevt <= 0 || !momenta_dev || !me_out_dev) return MG_ERR_ARG;
+  if (h->par.precision != MG_MIXED || !h->d->rows_mixed) return MG_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(momenta_dev) & 15u) return MG_ERR_ARG;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  mg::PhaseMarks marks;
+  int made = 0, rc = MG_OK;
+  for (; made < mg::PhaseMarks::MAX; made++)
+    if (cudaEventCreate(&marks.ev[made]) != cudaSuccess) {
+      rc = MG_ERR_CUDA;
+      break;
+    }
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (rc == MG_OK) {
+    std::lock_guard<std::mutex> lk(h->lock);
+    rc = mg_launch_sigma_locked(h, momenta_dev, nevt, me_out_dev, s, &marks);
+  }
+  if (rc == MG_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = MG_ERR_CUDA;
+  float t1 = 0.f, t2 = 0.f;
+  if (rc == MG_OK) {
+    for (int i = 0; i + 2 < marks.n; i += 2) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, marks.ev[i], marks.ev[i + 1]) != cudaSuccess ||
+          cudaEventElapsedTime(&b, marks.ev[i + 1], marks.ev[i + 2]) != cudaSuccess) {
+        rc = MG_ERR_CUDA;
+        break;
+      }
+      t1 += a;
+      t2 += b;
+    }
+  }
+  for (int i = 0; i < made; i++) cudaEventDestroy(marks.ev[i]);
+  if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+  if (rc != MG_OK) return rc;
+  if (ms_first) *ms_first = t1;
+  if (ms_second) *ms_second = t2;
+  if (slices) *slices = (marks.n - 1) / 2;
+  return MG_OK;
+}
+
+static_assert(MG_DIAG_WAIT_POLLS == mg::WAIT_POLLS, "default bound of the device waits");
+
+extern "C" int mg_diag_set_wait_polls(mg_process* h, uint32_t polls) {
+  if (!h) return MG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->lock);
+  h->kp.polls = polls;
+  return MG_OK;
 }
