@@ -53,7 +53,7 @@ def processes() -> list[str]:
 def generate() -> list[str]:
     """Write csrc/gen/<tag>.cuh, <tag>_f64.cu, <tag>_f32.cu and registry.cu; return the TUs."""
     sys.path.insert(0, ROOT)
-    from paper_2303_18244_gb300.generator.emit import PROCESSES, emit, emit_tu
+    from paper_2303_18244_gb300.generator.emit import PROCESSES, emit, emit_tu, header_name
     os.makedirs(GEN, exist_ok=True)
     tus = []
     procs = processes()
@@ -67,8 +67,11 @@ def generate() -> list[str]:
     _write_if_changed(path, "\n".join(reg))
     tus.append(path)
     for proc in procs:
-        tag, hdr = emit(proc)
-        _write_if_changed(os.path.join(GEN, f"{tag}.cuh"), hdr)
+        for prec in ("f64", "f32"):
+            name = header_name(proc, prec)
+            if prec == "f64" or name != header_name(proc, "f64"):
+                tag, hdr = emit(proc, prec)
+                _write_if_changed(os.path.join(GEN, name), hdr)
         for prec in ("f64", "f32"):
             _, tu = emit_tu(proc, prec)
             path = os.path.join(GEN, f"{tag}_{prec}.cu")

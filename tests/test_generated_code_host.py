@@ -92,7 +92,7 @@ def host_me(proc, real, workdir, header=None, vertices=None):
     """(momenta, |M|^2) of the generated code of proc compiled for the host
     in workdir; header / vertices replace the generated header or the text of
     mg_vertices.cuh (a copy in workdir is found before the original)."""
-    tag, generated = emit.emit(proc)
+    tag, generated = emit.emit(proc, "f32" if real == "float" else "f64")
     (workdir / f"{tag}.cuh").write_text(generated if header is None else header)
     if vertices is not None:
         (workdir / "mg_vertices.cuh").write_text(vertices)
@@ -131,16 +131,19 @@ def test_generated_code_on_the_host_matches_the_oracle(proc, real, tmp_path):
 
 
 def test_shared_current_chunk_order(tmp_path, monkeypatch):
-    """gg -> t t~ g g g with the chunks ordered by shared currents
-    (MG_CHUNK_ORDER=shared, not the default): a store of 87 crossing currents
-    instead of 241, and the same |M|^2 (FP64, within 1e-12 of the oracle)."""
+    """gg -> t t~ g g g: the FP32 header orders its chunks by shared currents
+    (a store of 87 crossing currents instead of the FP64 header's 241, its
+    struct in an inline namespace of its own), with the same |M|^2 (compiled
+    in FP64 here: within 1e-12 of the oracle)."""
     import re
+    monkeypatch.delenv("MG_CHUNK_ORDER", raising=False)
     proc = "g g > t t~ g g g"
-    _, default = emit.emit(proc)
-    monkeypatch.setenv("MG_CHUNK_ORDER", "shared")
-    _, shared = emit.emit(proc)
+    assert emit.header_name(proc, "f64") == "ggttggg.cuh" and emit.header_name(proc, "f32") == "ggttggg_f32.cuh"
+    _, default = emit.emit(proc, "f64")
+    _, shared = emit.emit(proc, "f32")
     store = [int(re.search(r"NSTORE = (\d+)", src).group(1)) for src in (default, shared)]
     assert store == [241, 87]
+    assert "inline namespace chunk_order_shared {" in shared and "inline namespace" not in default
     p, got = host_me(proc, "double", tmp_path, header=shared)
     ref = O.me(proc, p)
     assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-12
