@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
 FP64 path: relative error <= 1e-12 per event (the FP64 bar of the workload).
-Mixed path: median relative error <= 1e-5, with p99 and max bounded.
+Mixed path: per-process bounds on the median, p99 and max relative error
+(tests/mixed_bounds.py, about ten times the measured values).
 Small cases span several CTAs plus a ragged tail; the full workload sizes are
 checked on sampled events in the launch configuration bench.py times.
 """
@@ -13,6 +14,7 @@ torch = pytest.importorskip("torch")
 import oracle as O  # noqa: E402
 from paper_2303_18244_gb300 import mg  # noqa: E402
 from paper_2303_18244_gb300.inputs import process_momenta  # noqa: E402
+from mixed_bounds import MIXED_BOUNDS, check_mixed  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -109,9 +111,7 @@ def test_mixed_parity_small(proc):
     ref = O.me(proc, p)
     r = _rel(got, ref)
     print(f"{proc}: mixed rel err median {np.median(r):.2e} p99 {np.quantile(r, 0.99):.2e} max {r.max():.2e}")
-    assert np.median(r) <= 1e-5
-    assert np.quantile(r, 0.99) <= 1e-3
-    assert r.max() <= 1e-2
+    check_mixed(proc, r)
 
 
 @pytest.mark.parametrize("proc", PROCS, ids=_ids)
@@ -128,14 +128,17 @@ def test_full_size_sampled(proc, precision):
     got = _gpu_me(h, p)
     assert np.all(np.isfinite(got)) and np.all(got > 0)
     rng = np.random.default_rng(seed)
-    nsamp = 24 if proc == "g g > t t~ g g g" else 64
-    idx = np.unique(np.concatenate([[0, 127, 128, nfull - 1], rng.integers(0, nfull, nsamp)]))
+    nsamp = 300 if proc == "g g > t t~ g g g" else 200
+    # CTA edges (64- and 128-event blocks), the last full block and the tail
+    edges = [0, 63, 64, 127, 128, 255, 256, nfull - 129, nfull - 128, nfull - 2, nfull - 1]
+    idx = np.unique(np.concatenate([edges, rng.integers(0, nfull, nsamp)]))
     ref = O.me(proc, p[idx])
     r = _rel(got[idx], ref)
+    print(f"{proc} {precision}: sampled rel err median {np.median(r):.2e} max {r.max():.2e}")
     if precision == mg.MG_FP64:
         _assert_fp64(proc, p[idx], got[idx], ref)
     else:
-        assert np.median(r) <= 1e-5 and r.max() <= 1e-2
+        check_mixed(proc, r)
 
 
 def test_two_phase_mixed_across_slices():
@@ -158,7 +161,7 @@ def test_two_phase_mixed_across_slices():
     ref = _gpu_me(h64, p)
     r = _rel(got, ref)
     assert np.all(np.isfinite(got))
-    assert np.median(r) <= 1e-5 and r.max() <= 1e-2
+    check_mixed(proc, r)
     sub = _gpu_me(h, p[8000:8300])
     assert np.array_equal(sub, got[8000:8300])
 
@@ -379,8 +382,9 @@ def test_element_offsets_beyond_32_bits(proc, precision, nevt):
     if precision == mg.MG_FP64:
         _assert_fp64(proc, p, got, ref)
     else:
+        med, _, mx = MIXED_BOUNDS[proc]
         r = _rel(got, ref)
-        assert np.median(r) <= 1e-5 and r.max() <= 1e-2
+        assert np.median(r) <= med and r.max() <= mx
 
 
 def _rotate_onto_axis(p, slot, sign):
@@ -405,7 +409,7 @@ def _rotate_onto_axis(p, slot, sign):
     return q
 
 
-@pytest.mark.parametrize("proc", [p for p in PROCS if p != "g g > t t~ g g g"], ids=_ids)
+@pytest.mark.parametrize("proc", PROCS, ids=_ids)
 def test_final_state_along_the_beam_axis(proc):
     """Special kinematics: the top (mu- for e+e- -> mu+mu-) exactly along +z
     and along -z (p_T = 0), where the spinor set-up takes its degenerate
@@ -426,7 +430,8 @@ def test_final_state_along_the_beam_axis(proc):
     _assert_fp64(proc, p, got, ref)
     mixed = _gpu_me(mg.Process(proc, precision=mg.MG_MIXED), p)
     r = _rel(mixed, ref)
-    assert np.all(np.isfinite(mixed)) and np.median(r) <= 1e-5 and r.max() <= 1e-2
+    med, _, mx = MIXED_BOUNDS[proc]
+    assert np.all(np.isfinite(mixed)) and np.median(r) <= med and r.max() <= mx
 
 
 @pytest.mark.parametrize("proc,precision", [

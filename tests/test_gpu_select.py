@@ -10,7 +10,9 @@ from paper_2303_18244_gb300.inputs import process_momenta, uniforms  # noqa: E40
 
 pytestmark = pytest.mark.gpu
 
-CASES = [("g g > t t~", 1000.0, 2), ("g g > t t~ g", 1200.0, 6), ("g g > t t~ g g", 1500.0, 3)]
+# process, sqrt(s), seed, events
+CASES = [("g g > t t~", 1000.0, 2, 300), ("g g > t t~ g", 1200.0, 6, 300), ("g g > t t~ g g", 1500.0, 3, 300),
+         ("g g > t t~ g g g", 2000.0, 4, 130)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -45,9 +47,11 @@ def _expected_choice(weights, r):
     return k, margin
 
 
-@pytest.mark.parametrize("proc,sqrts,seed", CASES, ids=["ggtt", "ggttg", "ggttgg"])
-def test_fp64_choices_are_consistent(proc, sqrts, seed):
-    n = 300
+@pytest.mark.parametrize("proc,sqrts,seed,n", CASES, ids=["ggtt", "ggttg", "ggttgg", "ggttggg"])
+def test_fp64_choices_are_consistent(proc, sqrts, seed, n):
+    """FP64 choices against the per-helicity values and flow weights, and the
+    flow weights against the oracle's; for g g > t t~ g g g (128 helicities,
+    120 flows per event kept per thread) over two CTAs and a tail."""
     p = process_momenta(proc, sqrts, n, seed + 40)
     r = uniforms(77, 0, n, 1)[:, 0, :2]
     h = mg.Process(proc)
@@ -105,3 +109,25 @@ def test_eemumu_single_flow():
     me, hel, col, w = _run(h, p, r)
     assert np.all(col == 0) and np.all(mask[hel] == 1)
     np.testing.assert_allclose(me, O.me(proc, p), rtol=1e-12)
+
+
+def test_mixed_choices_valid_ggttggg():
+    """The mixed selection of g g > t t~ g g g: its ME within the mixed bounds
+    of the FP64 one, every chosen helicity good, every flow index in range,
+    the choices equal to the FP64 ones except where rounding crosses a
+    boundary."""
+    proc = "g g > t t~ g g g"
+    n = 256
+    p = process_momenta(proc, 2000.0, n, 10)
+    r = uniforms(80, 0, n, 1)[:, 0, :2]
+    h64 = mg.Process(proc)
+    hmx = mg.Process(proc, precision=mg.MG_MIXED)
+    cal = _dev(process_momenta(proc, 2000.0, 1024, 1004))
+    _, mask = mg.good_helicities(h64, cal)
+    mg.good_helicities(hmx, cal)
+    me64, hel64, col64, _ = _run(h64, p, r)
+    me, hel, col, _ = _run(hmx, p, r)
+    rel = np.abs(me / me64 - 1)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-3
+    assert np.all(mask[hel] == 1) and np.all((col >= 0) & (col < 120))
+    assert np.mean(hel == hel64) > 0.98 and np.mean(col == col64) > 0.98
