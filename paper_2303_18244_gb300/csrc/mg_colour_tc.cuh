@@ -507,9 +507,18 @@ __global__ void __launch_bounds__(128, 1)
 #ifndef MG_FLOWS_TMEM
 #define MG_FLOWS_TMEM 1
 #endif
-template <class P>
+// MG_FLOWS_NT: events per CTA of the tensor-memory flow kernel, 128 (two
+// CTAs of 4 warps per SM) or 256 (one CTA of 8 warps per SM holding all 512
+// TMEM columns: warp w keeps its 32 events in lanes 32 (w mod 4) and the
+// column half w / 4, so that with MG_CHUNK_SYNC all 8 warps of an SM run the
+// same chunk of the helicity program together)
+#ifndef MG_FLOWS_NT
+#define MG_FLOWS_NT 128
+#endif
+template <class P, int NT_ = MG_FLOWS_NT>
 struct LayoutFlowsTmem {
-  static constexpr int NT = 128;
+  static constexpr int NT = NT_;
+  static_assert(NT == 128 || NT == 256, "128 TMEM lanes, one or two column halves");
   static constexpr size_t r128(size_t b) { return ((b + 127) / 128) * 128; }
   static constexpr size_t bar_bytes = 128;  // TMA bar, TMEM address
   static constexpr size_t stage_bytes = size_t(NT) * P::NPAR * 4 * sizeof(double);
@@ -517,16 +526,16 @@ struct LayoutFlowsTmem {
   static constexpr size_t stage_off = bar_bytes;
   static constexpr size_t slab_off = stage_off + r128(stage_bytes);
   static constexpr size_t base_bytes = slab_off + r128(slab_bytes);
-  static constexpr uint32_t tmem_cols = 256;
+  static constexpr uint32_t tmem_cols = 256 * (NT / 128);
 };
 
 template <class P>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(MG_FLOWS_NT)
     flows_tmem_kernel(const double* __restrict__ mom, long long nevt, float2* __restrict__ J, long long ldj,
                       const int* __restrict__ hels, int nhel, KParams kp, unsigned* __restrict__ status) {
   using LY = LayoutFlowsTmem<P>;
-  constexpr int NT = 128;
-  static_assert(2 * P::NCOL <= (int)LY::tmem_cols, "flows fit in the allocated columns");
+  constexpr int NT = LY::NT;
+  static_assert(2 * P::NCOL <= 256, "flows fit in a column half");
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 16);
@@ -544,8 +553,9 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const FlowsTmem fl{tmem + ((uint32_t)(warp * 32) << 16)};
+  const FlowsTmem fl{tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(warp >> 2) * 256u};
   const long long e = (long long)blockIdx.x * NT + tid;
+  const bool in_rows = e < ldj;  // rows are padded to 128 events, the grid to NT
 #pragma unroll 1
   for (int ih = 0; ih < nhel; ih++) {
     const int h = __ldg(hels + ih);
@@ -559,7 +569,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int q = 0; q < 8; q++) {
         const int k = c / 2 + q;
-        if (k < P::NCOL) row[(long long)k * ldj] = make_float2(v[2 * q], v[2 * q + 1]);
+        if (k < P::NCOL && in_rows) row[(long long)k * ldj] = make_float2(v[2 * q], v[2 * q + 1]);
       }
     }
   }
@@ -720,7 +730,7 @@ template <class P, int NT>
 int launch_sigma_rows(const LaunchArgs& a) {
   static_assert(128 % NT == 0, "flow rows are padded to 128 events");
   constexpr bool tmem_flows = MG_FLOWS_TMEM != 0;
-  constexpr int NT1 = tmem_flows ? 128 : NT;
+  constexpr int NT1 = tmem_flows ? LayoutFlowsTmem<P>::NT : NT;
   constexpr size_t smem1 = tmem_flows ? LayoutFlowsTmem<P>::base_bytes : Layout<P, float, NT>::base_bytes;
   constexpr size_t smem2 = LayoutRows<P>::base_bytes;
   static const cudaError_t attr1 = [] {

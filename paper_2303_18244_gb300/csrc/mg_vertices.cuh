@@ -92,6 +92,47 @@ __device__ __forceinline__ cx<R> fma(R s, cx<R> b, cx<R> a) {
   return {a.re + s * b.re, a.im + s * b.im};
 }
 
+// MG_F32X2 (default 1): on sm_100 and later, the FP32 complex additions,
+// subtractions and real-scalar products use the paired FP32 instructions
+// (two lanes of FP32 in one instruction: the real and imaginary parts),
+// halving their instruction count.  Same IEEE rounding per lane as the scalar
+// forms.  Measured on gg -> t t~ g g mixed, 524288 events: 1.472e7 ->
+// 1.527e7 MEs/s, the same error distribution.  MG_F32X2_MUL=1 also pairs the
+// complex products, (ar, ar)(br, bi) + (-ai, ai)(bi, br), whose operands need
+// their lanes swapped or duplicated.
+#ifndef MG_F32X2
+#define MG_F32X2 1
+#endif
+#ifndef MG_F32X2_MUL
+#define MG_F32X2_MUL 0
+#endif
+#if MG_F32X2 && defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+__device__ __forceinline__ float2 f2_of(cx<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ cx<float> cx_of(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ cx<float> operator+(cx<float> a, cx<float> b) {
+  return cx_of(__fadd2_rn(f2_of(a), f2_of(b)));
+}
+__device__ __forceinline__ cx<float> operator-(cx<float> a, cx<float> b) {
+  return cx_of(__fadd2_rn(f2_of(a), make_float2(-b.re, -b.im)));
+}
+__device__ __forceinline__ cx<float> operator*(float s, cx<float> a) {
+  return cx_of(__fmul2_rn(make_float2(s, s), f2_of(a)));
+}
+__device__ __forceinline__ cx<float> fma(float s, cx<float> b, cx<float> a) {
+  return cx_of(__ffma2_rn(make_float2(s, s), f2_of(b), f2_of(a)));
+}
+#if MG_F32X2_MUL
+__device__ __forceinline__ cx<float> operator*(cx<float> a, cx<float> b) {
+  const float2 t = __fmul2_rn(make_float2(a.re, a.re), f2_of(b));
+  return cx_of(__ffma2_rn(make_float2(-a.im, a.im), make_float2(b.im, b.re), t));
+}
+__device__ __forceinline__ cx<float> fma(cx<float> b, cx<float> c, cx<float> a) {
+  const float2 t = __ffma2_rn(make_float2(b.re, b.re), f2_of(c), f2_of(a));
+  return cx_of(__ffma2_rn(make_float2(-b.im, b.im), make_float2(c.im, c.re), t));
+}
+#endif
+#endif
+
 template <typename R>
 __device__ __forceinline__ R fmaf_t(R a, R b, R c) {
   return a * b + c;
