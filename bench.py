@@ -9,9 +9,12 @@ with the good-helicity set-up (A0) done once before timing.  The headline
 value is the mixed-precision path; the FP64 path on the same events, the
 mixed-vs-FP64 accuracy, an end-to-end number through host buffers, the
 roofline of the dominant kernel and the FP64 CPU oracle's throughput on a
-bounded sample are reported beside it, with a short run (120 requests, mixed)
-of the continuous-batching request loop (Poisson arrivals, four processes,
-p50/p99 latency); --serve runs it with 2000 mixed and 200 FP64 requests.
+bounded sample are reported beside it, with the other workloads of the set
+(e+e- -> mu+mu-, g g -> t t~, g g -> t t~ g g g: mixed and FP64 throughput,
+each kernel's roofline fraction, accuracy against the oracle) under
+"configs", and a run of the continuous-batching request loop (Poisson
+arrivals, four processes, p50/p99 latency; 1000 mixed and 200 FP64 requests,
+--serve: 2000 and 400).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 
@@ -51,10 +54,13 @@ WORKLOADS = {
 METRIC = "gg→tt̄gg MEs/s on 1 GB300, FP64 vs mixed (≤1e-5 rel err); serve p50/p99 ms"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the mixed
-# kernel from one ncu capture of the current kernel on a small case: workload
-# -> (events captured, bytes); scaled to a launch by its events (the traffic
-# is per event: momenta in, |M|^2 out).  Set to None when the kernel changes.
-NCU_TRAFFIC = {"ggttgg": (65536, 12.802048e6 + 0.326912e6)}  # sigma_tc_kernel_ggttgg_mixed_65536ev.md (F)
+# kernel from one ncu capture (sigma_tc_kernel of g g -> t t~ g g, mixed,
+# 65536 events, one launch): workload -> (events captured, bytes, digest of
+# the kernel sources at capture time); scaled to a launch by its events (the
+# traffic is per event: momenta in, |M|^2 out).  Reported as null once the
+# sources differ from the captured ones (kernel_digest()).
+NCU_TRAFFIC = {"ggttgg": (65536, 12.802048e6 + 0.326912e6, None)}
+KERNEL_SOURCES = ("mg_kernels.cuh", "mg_vertices.cuh", "mg_colour_tc.cuh", "mg_flowstore.cuh")
 
 SERVE_PROCS = {  # process -> sqrt(s)
     "e+ e- > mu+ mu-": 500.0,
@@ -123,6 +129,34 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_digest(tag: str) -> str:
+    """sha256 (16 hex digits) of the hand-written kernel sources and of the
+    process's flop count (which changes with its generated code)."""
+    import hashlib
+    d = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2303_18244_gb300", "csrc", f), "rb") as fh:
+            d.update(fh.read())
+    d.update(json.dumps(load_flops(tag), sort_keys=True).encode())
+    return d.hexdigest()[:16]
+
+
+def traffic_per_launch(tag: str, nevt: int):
+    cap = NCU_TRAFFIC.get(tag)
+    if cap is None or cap[2] != kernel_digest(tag):
+        return None
+    return cap[1] * nevt / cap[0]
+
+
+def measured_peak(key: str):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def load_flops(tag: str) -> dict:
@@ -218,7 +252,8 @@ def main():
     ap.add_argument("--nevt", type=int, default=None)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--serve", action="store_true",
-                    help="full serving benchmark (2000 mixed and 200 FP64 requests) instead of the short mixed one")
+                    help="longer serving benchmark (2000 mixed and 400 FP64 requests instead of 1000 and 200)")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads of the set")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -384,8 +419,7 @@ def main():
     peak64 = mg.diag_fma_peak(1) / 1e3
     achieved64 = flops_evt * nevt / (t_64 * 1e-3) / 1e12
 
-    cap = NCU_TRAFFIC.get(args.proc)
-    traffic = None if cap is None else cap[1] * nevt / cap[0]
+    traffic = traffic_per_launch(args.proc, nevt)
 
     res = {
         "metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": world, "steps": args.steps,
@@ -456,10 +490,14 @@ def main():
                 acc[name]["beyond_1e-12"] = int(bad.size)
                 acc[name]["max_adjudicated"] = float(r_adj.max())
         res["accuracy_vs_oracle"] = acc
+    if not args.no_configs and args.proc == "ggttgg" and world == 1:  # one GPU: the set's other workloads
+        res["configs"] = {t: measure_config(t, mg, process_momenta, timed_call, peak32, peak64)
+                          for t in ("eemumu", "ggtt", "ggttggg")}
     if not args.no_serve and args.proc == "ggttgg":
-        nreq = args.serve_requests or (2000 if args.serve else 120)
-        plan = {"mixed": nreq, "fp64": max(1, nreq // 10)} if args.serve else {"mixed": nreq}
-        res["serve"] = serve_bench(plan, mg, process_momenta)
+        nreq = args.serve_requests or (2000 if args.serve else 1000)
+        plan = {"mixed": nreq, "fp64": max(1, nreq // 5)}
+        paced = {"mixed": max(1, nreq // 2), "fp64": max(1, nreq // 4)}
+        res["serve"] = serve_bench(plan, mg, process_momenta, paced)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
@@ -467,12 +505,133 @@ def main():
     return 0
 
 
-def serve_bench(plan, mg, process_momenta):
+def measure_config(tag, mg, process_momenta, timed_call, peak32, peak64, oracle_budget_s=3.0):
+    """One workload of the set, mixed and FP64: MEs/s from CUDA-event-timed
+    steps (median of 3 after warm-up, L2 flushed before each), the roofline
+    fraction of its kernels, and the per-event error of both paths against the
+    oracle on the workload's first events (as many as the oracle evaluates in
+    about oracle_budget_s on the host cores)."""
+    import torch
+    proc, sqrts, seed, nevt = WORKLOADS[tag]
+    p = process_momenta(proc, sqrts, nevt, seed)
+    mom = torch.from_numpy(p).cuda()
+    calib = torch.from_numpy(process_momenta(proc, sqrts, 1024, seed + 1000)).cuda()
+    fl = load_flops(tag)
+    res = {"workload": f"{proc}, {nevt} events at sqrt(s)={sqrts:.0f} GeV, seed {seed}"}
+    outs = {}
+    for name, prec, warm in (("mixed", mg.MG_MIXED, 3), ("fp64", mg.MG_FP64, 1)):
+        h = mg.Process(proc, precision=prec)
+        ngood, _ = mg.good_helicities(h, calib)
+        out = torch.empty(nevt, dtype=torch.float64, device="cuda")
+        ms = timed_call(lambda: mg.sigma(h, mom, out), 3, warm)
+        assert mg.process_status(h) == 0
+        t = statistics.median(ms)
+        flops = ngood * (fl["amp_flops_per_hel"] + fl["colour_dense_flops_per_hel"]) * nevt
+        peak = peak32 if name == "mixed" else peak64
+        r = {"value": nevt / (t * 1e-3), "unit": "MEs/s", "ms_per_step": t, "steps": len(ms),
+             "good_helicities": ngood,
+             "roofline": {"bound": "alu", "achieved": flops / (t * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                          "frac": flops / (t * 1e-3) / 1e12 / peak,
+                          "peak_source": f"measured {'FP32' if name == 'mixed' else 'FP64'} FMA loop (mg_diag)"}}
+        if name == "mixed" and tag == "ggttggg":
+            r["kernels"] = two_phase_rooflines(h, mom, out, mg, fl, ngood, nevt)
+        res[name] = r
+        outs[name] = out.cpu().numpy()
+        h.close()
+    res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
+    # accuracy against the oracle on the first events
+    _, cores, n, dt, _, ref = time_oracle(proc, sqrts, seed, 0, budget_s=oracle_budget_s, one_core=False,
+                                          max_events=nevt)
+    acc = {"events": int(n), "sample": f"the first {n} events ({dt:.1f} s of the oracle on {cores} cores)"}
+    for name in ("fp64", "mixed"):
+        got = outs[name][:n]
+        r = np.abs(got - ref) / np.abs(ref)
+        acc[name] = {"median": float(np.median(r)), "p99": float(np.quantile(r, 0.99)), "max": float(r.max())}
+        if name == "fp64":
+            import oracle as O
+            bad = np.nonzero(r > 1e-12)[0]
+            if bad.size:
+                ext = O.me(proc, p[:n][bad], extended=True)
+                r = r.copy()
+                r[bad] = np.abs(got[bad] - ext) / np.abs(ext)
+            acc[name]["beyond_1e-12"] = int(bad.size)
+            acc[name]["max_adjudicated"] = float(r.max())
+    res["accuracy_vs_oracle"] = acc
+    return res
+
+
+def two_phase_rooflines(h, mom, out, mg, fl, ngood, nevt):
+    """The two kernels of the two-phase mixed g g -> t t~ g g g call timed one
+    by one (CUDA events between the launches, mg_diag_sigma_phases; median of
+    3 calls): the flow kernel against the FP32 FMA peak (amplitude flops), the
+    tensor-core colour kernel against HBM (it reads every helicity-event row
+    of 120 complex FP32 flows once: 960 B per row) and, beside it, its
+    tensor-pipe fraction (4 * 120^2 flop per row, the dense quadratic form)
+    against the measured BF16 GEMM peak (FP16 runs at the BF16 rate)."""
+    runs = [mg.diag_sigma_phases(h, mom, out) for _ in range(3)]
+    t1 = statistics.median(r[0] for r in runs)
+    t2 = statistics.median(r[1] for r in runs)
+    slices = runs[0][2]
+    rows = ngood * ((nevt + 127) // 128 * 128)
+    peak32 = mg.diag_fma_peak(0) / 1e3
+    hbm = measured_peak("hbm_gbs")
+    bf16 = measured_peak("bf16_tflops")
+    f1 = ngood * fl["amp_flops_per_hel"] * nevt / (t1 * 1e-3) / 1e12
+    b2 = rows * 120 * 8 / (t2 * 1e-3) / 1e9
+    f2 = 4 * 120 ** 2 * ngood * nevt / (t2 * 1e-3) / 1e12
+    return {
+        "slices": slices,
+        "flows_tmem_kernel": {"ms": t1, "bound": "alu", "achieved": f1, "peak": peak32, "unit": "TFLOP/s",
+                              "frac": f1 / peak32, "peak_source": "measured FP32 FMA loop (mg_diag)"},
+        "colour_rows_tc_kernel": {"ms": t2, "bound": "hbm", "achieved": b2, "peak": hbm, "unit": "GB/s",
+                                  "frac": b2 / hbm if hbm else None,
+                                  "bytes_per_row": "960 (120 complex FP32 flows read once)",
+                                  "peak_source": "measured copy bandwidth (hbm_gbs)",
+                                  "tensor": {"achieved": f2, "peak": bf16, "unit": "TFLOP/s",
+                                             "frac": f2 / bf16 if bf16 else None,
+                                             "flop_per_row": "4 * 120^2",
+                                             "peak_source": "measured BF16 GEMM burst (FP16 at the BF16 rate)"}},
+    }
+
+
+def serve_run(srv, handles, reqs, gap_scale=1.0):
+    """Submit reqs (process, events, gap s, momenta, output) at their Poisson
+    gaps times gap_scale, wait for every result; latency = submit -> done."""
+    ids = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for proc, n, gap, mom, me in reqs:
+        t_next += gap * gap_scale
+        while time.perf_counter() < t_next:
+            pass
+        ids.append(srv.submit(handles[proc], mom, me))
+    lat, tot = [], 0
+    for rid, (proc, n, *_rest) in zip(ids, reqs):
+        while True:
+            rc, st = srv.poll(rid, 1000000)
+            if rc == 0:
+                break
+        lat.append(st.latency_us / 1e3)
+        tot += n
+    wall = time.perf_counter() - t0
+    window = gap_scale * sum(r[2] for r in reqs)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "MEs_per_s": tot / wall, "requests": len(reqs), "events": tot,
+            "mean_gap_ms": 1e3 * window / len(reqs), "offered_MEs_per_s": tot / window, "wall_s": wall}
+
+
+def serve_bench(plan, mg, process_momenta, paced=None, utilisation=0.7):
     """Poisson arrivals (mean gap 2 ms) of requests drawn uniformly from four
     processes, log-uniform 256..65536 events each (Philox seed 5 drives the
     choices), served by the continuous-batching loop; p50/p99 latency.
-    plan: precision name -> number of requests."""
+    plan: precision name -> number of requests.  The workload offers several
+    times the events per second one GPU evaluates (its gg -> t t~ g g g
+    requests alone), so its latency is mostly time in the queue; with paced
+    (precision name -> number of requests) the first requests are served again
+    with every gap stretched so that the offered rate is `utilisation` times
+    the rate the first run achieved: the latency of a loop that keeps up."""
     from paper_2303_18244_gb300.inputs import uniforms
+    import torch
     out = {}
     for prec_name, prec in (("mixed", mg.MG_MIXED), ("fp64", mg.MG_FP64)):
         if prec_name not in plan:
@@ -481,7 +640,6 @@ def serve_bench(plan, mg, process_momenta):
         handles = {p: mg.Process(p, precision=prec) for p in SERVE_PROCS}
         for p, hh in handles.items():
             calib = process_momenta(p, SERVE_PROCS[p], 1024, 1005)
-            import torch
             mg.good_helicities(hh, torch.from_numpy(calib).cuda())
         u = uniforms(5, 0, nreq, 1)[:, 0, :]
         reqs = []
@@ -489,32 +647,26 @@ def serve_bench(plan, mg, process_momenta):
             proc = list(SERVE_PROCS)[min(3, int(u[i, 0] * 4))]
             n = int(round(math.exp(math.log(256) + u[i, 1] * (math.log(65536) - math.log(256)))))
             gap = -2e-3 * math.log(u[i, 2])
-            mom = process_momenta(proc, SERVE_PROCS[proc], n, 5, first_event=i * 65536)
-            reqs.append((proc, n, gap, mom, np.empty(n)))
+            # the request's RAMBO events (seed 5, its own block of the stream),
+            # generated on the device and handed to the client in host memory
+            d = torch.empty((n, handles[proc].info.npar, 4), dtype=torch.float64, device="cuda")
+            mg.rambo(handles[proc], SERVE_PROCS[proc], 5, i * 65536, d)
+            reqs.append((proc, n, gap, d.cpu().numpy(), np.empty(n)))
         srv = mg.Server()
-        ids = []
-        t0 = time.perf_counter()
-        t_next = t0
-        for proc, n, gap, mom, me in reqs:
-            t_next += gap
-            while time.perf_counter() < t_next:
-                pass
-            ids.append(srv.submit(handles[proc], mom, me))
-        lat = []
-        tot = 0
-        for rid, (proc, n, *_rest) in zip(ids, reqs):
-            while True:
-                rc, st = srv.poll(rid, 1000000)
-                if rc == 0:
-                    break
-            lat.append(st.latency_us / 1e3)
-            tot += n
-        wall = time.perf_counter() - t0
+        r = serve_run(srv, handles, reqs)
+        r["utilisation_offered"] = r["offered_MEs_per_s"] / r["MEs_per_s"]
+        r["workload"] = ("Poisson arrivals (mean 2 ms), processes uniform over "
+                         "ee->mumu/gg->tt~/gg->tt~gg/gg->tt~ggg, log-uniform 256-65536 events, seed 5")
+        out[prec_name] = r
+        if paced and prec_name in paced:
+            sub = reqs[: paced[prec_name]]
+            scale = r["utilisation_offered"] / utilisation
+            rp = serve_run(srv, handles, sub, gap_scale=scale)
+            rp["utilisation_target"] = utilisation
+            rp["workload"] = (f"the first {len(sub)} requests of the same stream, every gap times {scale:.1f} "
+                              f"(offered rate {utilisation} of the rate served above)")
+            out[prec_name + "_paced"] = rp
         srv.close()
-        out[prec_name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                          "MEs_per_s": tot / wall, "requests": len(reqs), "events": tot,
-                          "workload": "Poisson arrivals (mean 2 ms), processes uniform over "
-                                      "ee->mumu/gg->tt~/gg->tt~gg/gg->tt~ggg, log-uniform 256-65536 events, seed 5"}
     return out
 
 
