@@ -33,6 +33,7 @@ PROCS = {
     "g g > t t~ g g g": 4,
     "u u~ > t t~": 5,
     "u u~ > t t~ g": 6,
+    "u u~ > t t~ g g": 7,
 }
 
 
@@ -94,6 +95,8 @@ def _declare(L):
     L.mgo_npar.argtypes = [ctypes.c_int]
     L.mgo_flow_weights.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int64, _D]
     L.mgo_uuttg_amps.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+    L.mgo_uutt_ng.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int64, _D]
+    L.mgo_uutt_ng_fixed_pol.argtypes = [ctypes.c_int, _D, _D, _D, _D]
     return L
 
 
@@ -263,3 +266,43 @@ def uuttg_amps(mom: np.ndarray, spins, eps5, params: Params | None = None) -> np
     out = np.empty(648 * 2, dtype=np.float64)
     _check(lib().mgo_uuttg_amps(_p(params.array()), _p(m), *[int(x) for x in spins], _p(e), _p(out)))
     return out.view(np.complex128).reshape(3, 3, 3, 3, 8)
+
+
+def uutt_ng(ng: int, momenta: np.ndarray, params: Params | None = None, threads: int | None = None,
+            extended: bool = False) -> np.ndarray:
+    """u u~ -> t t~ + ng gluons (0..2) by the colour-dressed recursion over
+    both quark lines (mgo_uutt_ng), events split over host threads."""
+    params = params or Params()
+    mom = np.ascontiguousarray(momenta, dtype=np.float64)
+    nevt = mom.shape[0]
+    out = np.empty(nevt, dtype=np.float64)
+    pa = params.array()
+    L = lib_ext() if extended else lib()
+    threads = max(1, min(threads or os.cpu_count() or 1, nevt))
+    bounds = np.linspace(0, nevt, threads + 1).astype(np.int64)
+
+    def run(i):
+        a, b = int(bounds[i]), int(bounds[i + 1])
+        if b > a:
+            sub_m = np.ascontiguousarray(mom[a:b])
+            sub_o = np.empty(b - a, dtype=np.float64)
+            _check(L.mgo_uutt_ng(ng, _p(pa), _p(sub_m), b - a, _p(sub_o)))
+            out[a:b] = sub_o
+
+    if threads == 1:
+        run(0)
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, range(threads)))
+    return out
+
+
+def uutt_ng_fixed_pol(ng: int, mom: np.ndarray, eps, params: Params | None = None) -> float:
+    """|M|^2 of u u~ -> t t~ + ng gluons summed over quark spins and colours,
+    for given complex gluon polarisation vectors eps[ng][4] (eps = k: Ward)."""
+    params = params or Params()
+    m = np.ascontiguousarray(mom, dtype=np.float64).reshape(-1)
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.complex128).reshape(ng, 4).view(np.float64))
+    out = np.empty(1, dtype=np.float64)
+    _check(lib().mgo_uutt_ng_fixed_pol(ng, _p(params.array()), _p(m), _p(e), _p(out)))
+    return float(out[0])

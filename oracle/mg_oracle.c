@@ -20,6 +20,10 @@
  *     with explicit 4x4 Dirac matrices;
  *   - u u~ -> t t~: the s-channel gluon diagram with explicit Dirac matrices
  *     and an explicit sum over every colour index;
+ *   - u u~ -> t t~ g g: colour-dressed Berends-Giele recursion over both
+ *     quark lines with explicit T^a and f^{abc}, every colour summed (the
+ *     same recursion reproduces the u u~ -> t t~ and u u~ -> t t~ g results
+ *     of the independent evaluations);
  *   - g g -> t t~ + (n-2) g: colour decomposition on one quark line,
  *       M = sum_{sigma in S_n} (T^{a_sigma1} ... T^{a_sigman})_{i_t j_tbar} A(sigma),
  *     partial amplitudes A(sigma) from colour-ordered Berends-Giele recursion
@@ -69,7 +73,16 @@ static const real PI_R = 3.14159265358979323846264338327950288L;
 #define MGO_ERR_ARG (-1)
 #define MGO_ERR_NOMEM (-2)
 
-enum { MGO_EEMUMU = 0, MGO_GGTT = 1, MGO_GGTTG = 2, MGO_GGTTGG = 3, MGO_GGTTGGG = 4, MGO_UUTT = 5, MGO_UUTTG = 6 };
+enum {
+  MGO_EEMUMU = 0,
+  MGO_GGTT = 1,
+  MGO_GGTTG = 2,
+  MGO_GGTTGG = 3,
+  MGO_GGTTGGG = 4,
+  MGO_UUTT = 5,
+  MGO_UUTTG = 6,
+  MGO_UUTTGG = 7
+};
 
 #define MAXG 5     /* at most 5 gluons */
 #define MAXPERM 120
@@ -1086,6 +1099,395 @@ int mgo_uuttg_amps(const double* params, const double* mom, int s1, int s2, int 
   return MGO_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* u u~ -> t t~ + n gluons (n <= 2): colour-dressed Berends-Giele       */
+/* recursion over both quark lines                                    */
+/* ------------------------------------------------------------------ */
+
+/* Legs: 0 u (incoming, the root of the recursion), 1 u~ (incoming), 2 t, 3 t~,
+ * 4.. gluons (outgoing).  Off-shell currents are built over subsets S of the
+ * legs 1.. (bit leg-1), with the Feynman rules of the header:
+ *   gluon current  J^c(S)    no u~, both or neither of t, t~: the three- and
+ *                            four-gluon vertices, and the top line closed by
+ *                            i g gamma^mu T^c;  times -i/P^2
+ *   light row      Ubar_m(S) holds u~ (and possibly the closed top line)
+ *   top row        Tbar_m(S) holds t,  top column T_m(S) holds t~
+ *   quark propagator i (Qslash + m) / (Q^2 - m^2 + i m Gamma) (top), i Qslash/Q^2 (u)
+ * Each current carries its off-shell colour (c < 8 or m < 3) and, as a plain
+ * array index x = 9 j + 3 k + l, the colours j, k, l of the external u~, t,
+ * t~; a current that does not hold one of those legs is the same for every
+ * value of its index, so products of two currents are taken entrywise in x.
+ * The amplitude M[i][x] for the u colour i closes at the root:
+ *   M = sum_{A u B} Ubar_m(A) (i g Jslash^c(B) T^c_{m i}) u(p1).
+ * The gluon colours are fixed per evaluation and summed outside. */
+#define QQ_LEGS 6
+#define QQ_X 27
+typedef struct {
+  cplx v[8][QQ_X][4];
+  int have, nz; /* computed; some entry non-zero */
+} qq_cur;
+
+typedef struct {
+  int nleg;                 /* legs 1 .. nleg-1 below the root            */
+  real g, mt, wt;
+  real kin[QQ_LEGS][4];     /* incoming momentum of each leg              */
+  cplx eps[QQ_LEGS][4];     /* gluon polarisations (legs >= 4)            */
+  int col[QQ_LEGS];         /* gluon colours (legs >= 4)                  */
+  cplx u1[4], vb2[4], ub3[4], v4[4];
+  qq_cur c[1 << (QQ_LEGS - 1)];
+} qq_ws;
+
+static int qq_kind(int S) {
+  /* 1 gluon, 2 light row, 3 top row, 4 top column, 0 none */
+  const int has1 = S & 1, has2 = (S >> 1) & 1, has3 = (S >> 2) & 1;
+  if (!has1 && has2 == has3) return 1;
+  if (has1 && has2 == has3) return 2;
+  if (!has1 && has2 && !has3) return 3;
+  if (!has1 && !has2 && has3) return 4;
+  return 0;
+}
+
+static void qq_momentum(const qq_ws* w, int S, real K[4]) {
+  for (int mu = 0; mu < 4; mu++) K[mu] = 0.0;
+  for (int b = 0; b < w->nleg - 1; b++)
+    if (S & (1 << b))
+      for (int mu = 0; mu < 4; mu++) K[mu] += w->kin[b + 1][mu];
+}
+
+static void qq_current(qq_ws* w, int S);
+
+/* row (off-shell colour m) times i g Jslash^c T^c_{m n}, summed over c, m, into acc[n][x] */
+static void qq_row_times_gluon(const qq_cur* R, const qq_cur* G, const real g, cplx acc[3][QQ_X][4]) {
+  for (int c = 0; c < 8; c++)
+    for (int x = 0; x < QQ_X; x++) {
+      const cplx* j = G->v[c][x];
+      if (j[0] == 0 && j[1] == 0 && j[2] == 0 && j[3] == 0) continue;
+      cplx Sl[4][4];
+      slash_c(j, Sl);
+      for (int m = 0; m < 3; m++) {
+        const cplx* r = R->v[m][x];
+        if (r[0] == 0 && r[1] == 0 && r[2] == 0 && r[3] == 0) continue;
+        cplx t[4];
+        rowmat(r, (const cplx(*)[4])Sl, t);
+        for (int n = 0; n < 3; n++) {
+          const cplx tc = TGEN[c][m][n];
+          if (tc == 0) continue;
+          for (int s = 0; s < 4; s++) acc[n][x][s] += I * g * tc * t[s];
+        }
+      }
+    }
+}
+
+static void qq_current(qq_ws* w, int S) {
+  qq_cur* cur = &w->c[S];
+  if (cur->have) return;
+  cur->have = 1;
+  const int kind = qq_kind(S);
+  memset(cur->v, 0, (kind == 1 ? 8 : 3) * sizeof(cur->v[0]));
+  const int low = S & (-S);
+  const real g = w->g;
+  if (__builtin_popcount(S) == 1) {
+    const int leg = __builtin_ctz(S) + 1;
+    for (int x = 0; x < QQ_X; x++) {
+      const int j = x / 9, k = (x / 3) % 3, l = x % 3;
+      for (int s = 0; s < 4; s++) {
+        if (leg == 1) cur->v[j][x][s] = w->vb2[s];
+        else if (leg == 2) cur->v[k][x][s] = w->ub3[s];
+        else if (leg == 3) cur->v[l][x][s] = w->v4[s];
+        else cur->v[w->col[leg]][x][s] = w->eps[leg][s];
+      }
+    }
+    cur->nz = 1;
+    return;
+  }
+  real K[4];
+  qq_momentum(w, S, K);
+  if (kind == 1) {
+    cplx acc[8][QQ_X][4]; /* per recursion level: sub-currents are built inside the loops */
+    memset(acc, 0, sizeof(acc));
+    /* three-gluon vertex, unordered pairs of gluon currents */
+    for (int A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+      if (!(A & low)) continue;
+      const int B = S ^ A;
+      if (qq_kind(A) != 1 || qq_kind(B) != 1) continue;
+      qq_current(w, A);
+      qq_current(w, B);
+      if (!w->c[A].nz || !w->c[B].nz) continue;
+      real KA[4], KB[4];
+      qq_momentum(w, A, KA);
+      qq_momentum(w, B, KB);
+      for (int a = 0; a < 8; a++)
+        for (int b = 0; b < 8; b++) {
+          int any = 0;
+          for (int c = 0; c < 8; c++) any |= FABC[a][b][c] != 0.0;
+          if (!any) continue;
+          for (int x = 0; x < QQ_X; x++) {
+            const cplx* ja = w->c[A].v[a][x];
+            const cplx* jb = w->c[B].v[b][x];
+            if ((ja[0] == 0 && ja[1] == 0 && ja[2] == 0 && ja[3] == 0) ||
+                (jb[0] == 0 && jb[1] == 0 && jb[2] == 0 && jb[3] == 0))
+              continue;
+            cplx t[4];
+            vertex3(KA, ja, KB, jb, t);
+            for (int c = 0; c < 8; c++) {
+              const real f = FABC[a][b][c];
+              if (f == 0.0) continue;
+              for (int mu = 0; mu < 4; mu++) acc[c][x][mu] += -I * g * f * t[mu]; /* (-i/P^2) g f V3 */
+            }
+          }
+        }
+    }
+    /* four-gluon vertex, unordered triples of gluon currents (as in the
+     * one-line colour-dressed recursion above) */
+    for (int A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+      if (!(A & low)) continue;
+      const int R = S ^ A;
+      const int low2 = R & (-R);
+      for (int B = (R - 1) & R; B > 0; B = (B - 1) & R) {
+        if (!(B & low2)) continue;
+        const int C = R ^ B;
+        if (qq_kind(A) != 1 || qq_kind(B) != 1 || qq_kind(C) != 1) continue;
+        qq_current(w, A);
+        qq_current(w, B);
+        qq_current(w, C);
+        for (int a = 0; a < 8; a++)
+          for (int b = 0; b < 8; b++)
+            for (int d = 0; d < 8; d++)
+              for (int x = 0; x < QQ_X; x++) {
+                const cplx* j1 = w->c[A].v[a][x];
+                const cplx* j2 = w->c[B].v[b][x];
+                const cplx* j3 = w->c[C].v[d][x];
+                const cplx d12 = dot_cc(j1, j2), d13 = dot_cc(j1, j3), d23 = dot_cc(j2, j3);
+                if (d12 == 0 && d13 == 0 && d23 == 0) continue;
+                for (int c = 0; c < 8; c++) {
+                  real f1 = 0, f2 = 0, f3 = 0;
+                  for (int e = 0; e < 8; e++) {
+                    f1 += FABC[a][b][e] * FABC[d][c][e];
+                    f2 += FABC[a][d][e] * FABC[b][c][e];
+                    f3 += FABC[a][c][e] * FABC[b][d][e];
+                  }
+                  if (f1 == 0 && f2 == 0 && f3 == 0) continue;
+                  for (int mu = 0; mu < 4; mu++) {
+                    const cplx lor = f1 * (d13 * j2[mu] - d23 * j1[mu]) + f2 * (d12 * j3[mu] - d23 * j1[mu]) +
+                                     f3 * (d12 * j3[mu] - d13 * j2[mu]);
+                    acc[c][x][mu] += -g * g * lor; /* (-i/P^2) (-i g^2) */
+                  }
+                }
+              }
+      }
+    }
+    /* the top line closed into the gluon: Tbar_m(A) (i g gamma^mu T^c_{mn}) T_n(B) */
+    if (S & 2) {
+      for (int A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+        const int B = S ^ A;
+        if (qq_kind(A) != 3 || qq_kind(B) != 4) continue;
+        qq_current(w, A);
+        qq_current(w, B);
+        for (int x = 0; x < QQ_X; x++)
+          for (int m = 0; m < 3; m++)
+            for (int n = 0; n < 3; n++) {
+              const cplx* r = w->c[A].v[m][x];
+              const cplx* cc = w->c[B].v[n][x];
+              for (int mu = 0; mu < 4; mu++) {
+                cplx t[4];
+                matcol((const cplx(*)[4])GAM[mu], cc, t);
+                const cplx rv = rowcol(r, t);
+                if (rv == 0) continue;
+                for (int c = 0; c < 8; c++) {
+                  const cplx tc = TGEN[c][m][n];
+                  if (tc != 0) acc[c][x][mu] += g * tc * rv; /* (-i/P^2) (i g) */
+                }
+              }
+            }
+      }
+    }
+    const real p2 = dot_rr(K, K);
+    int nz = 0;
+    for (int c = 0; c < 8; c++)
+      for (int x = 0; x < QQ_X; x++)
+        for (int mu = 0; mu < 4; mu++) {
+          cur->v[c][x][mu] = acc[c][x][mu] / p2;
+          nz |= acc[c][x][mu] != 0;
+        }
+    cur->nz = nz;
+    return;
+  }
+  /* quark lines: the leg at the line's end plus gluon currents attached */
+  cplx acc3[3][QQ_X][4];
+  memset(acc3, 0, sizeof(acc3));
+  const int end = (kind == 2) ? 1 : (kind == 3) ? 2 : 4; /* bit of the line's external leg */
+  real Q[4];
+  for (int A = (S - 1) & S; A > 0; A = (A - 1) & S) {
+    if (!(A & end)) continue;
+    const int B = S ^ A;
+    if (qq_kind(A) != kind || qq_kind(B) != 1) continue;
+    qq_current(w, A);
+    qq_current(w, B);
+    if (!w->c[A].nz || !w->c[B].nz) continue;
+    if (kind != 4) {
+      qq_row_times_gluon(&w->c[A], &w->c[B], g, acc3);
+    } else {
+      /* column: T^c_{m n} (i g Jslash^c) T_n(A) */
+      for (int c = 0; c < 8; c++)
+        for (int x = 0; x < QQ_X; x++) {
+          const cplx* j = w->c[B].v[c][x];
+          if (j[0] == 0 && j[1] == 0 && j[2] == 0 && j[3] == 0) continue;
+          cplx Sl[4][4];
+          slash_c(j, Sl);
+          for (int n = 0; n < 3; n++) {
+            cplx t[4];
+            matcol((const cplx(*)[4])Sl, w->c[A].v[n][x], t);
+            for (int m = 0; m < 3; m++) {
+              const cplx tc = TGEN[c][m][n];
+              if (tc == 0) continue;
+              for (int s = 0; s < 4; s++) acc3[m][x][s] += I * g * tc * t[s];
+            }
+          }
+        }
+    }
+  }
+  /* propagator momentum along the fermion flow: rows end at t (p3) or at the
+   * incoming u~ (-p2), columns start at the outgoing t~ (-p4); every attached
+   * current adds its incoming momentum with the sign of the flow */
+  const real* kend = w->kin[__builtin_ctz(end) + 1];
+  for (int mu = 0; mu < 4; mu++) {
+    const real attached = K[mu] - kend[mu];
+    Q[mu] = (kind == 4) ? (kend[mu] + attached) : (-kend[mu] - attached);
+  }
+  const real m = (kind == 2) ? 0.0 : w->mt;
+  const cplx den = dot_rr(Q, Q) - m * m + ((kind == 2) ? 0.0 : I * m * w->wt);
+  cplx P[4][4];
+  slash_r(Q, P);
+  for (int r = 0; r < 4; r++) P[r][r] += m;
+  int nz = 0;
+  for (int c = 0; c < 3; c++)
+    for (int x = 0; x < QQ_X; x++) {
+      cplx t[4];
+      if (kind == 4) matcol((const cplx(*)[4])P, acc3[c][x], t);
+      else rowmat(acc3[c][x], (const cplx(*)[4])P, t);
+      for (int s = 0; s < 4; s++) {
+        cur->v[c][x][s] = (I / den) * t[s];
+        nz |= t[s] != 0;
+      }
+    }
+  cur->nz = nz;
+}
+
+/* sum over all external colours of |M|^2 for the spin states and gluon
+ * polarisations set in w (the gluon colours are summed here) */
+static real qq_colour_sum(qq_ws* w) {
+  const int ng = w->nleg - 4;
+  const int full = (1 << (w->nleg - 1)) - 1;
+  int ncol = 1;
+  for (int i = 0; i < ng; i++) ncol *= 8;
+  real sum = 0.0;
+  for (int code = 0; code < ncol; code++) {
+    int cc = code;
+    for (int i = 0; i < ng; i++) {
+      w->col[4 + i] = cc % 8;
+      cc /= 8;
+    }
+    for (int S = 0; S <= full; S++) w->c[S].have = 0;
+    cplx M[3][QQ_X];
+    memset(M, 0, sizeof(M));
+    for (int A = full; A > 0; A = (A - 1) & full) {
+      if (!(A & 1)) continue;
+      const int B = full ^ A;
+      if (B == 0 || qq_kind(A) != 2 || qq_kind(B) != 1) continue;
+      qq_current(w, A);
+      qq_current(w, B);
+      cplx acc[3][QQ_X][4];
+      memset(acc, 0, sizeof(acc));
+      qq_row_times_gluon(&w->c[A], &w->c[B], w->g, acc);
+      for (int i = 0; i < 3; i++)
+        for (int x = 0; x < QQ_X; x++) M[i][x] += rowcol(acc[i][x], w->u1);
+    }
+    for (int i = 0; i < 3; i++)
+      for (int x = 0; x < QQ_X; x++) sum += creal(M[i][x] * conj(M[i][x]));
+  }
+  return sum;
+}
+
+/* u(p1) u~(p2) -> t(p3) t~(p4) + ng gluons (p5, p6): every spin state of the
+ * quarks (Dirac-representation spin-z spinors) and every linear polarisation
+ * of the gluons, every colour; IDEN = 4 spins x 9 colours x ng!.  If eps_in
+ * is not NULL it replaces the gluon polarisations (complex [ng][4], one spin
+ * state of the gluons) and the result is the sum over quark spins only. */
+static real me_uutt_ng(const oparams* o, int ng, const real* mom, const cplx* eps_in) {
+  if (ng < 0 || ng > 2) return NAN;
+  init_fabc();
+  qq_ws* w = (qq_ws*)malloc(sizeof(qq_ws));
+  if (!w) return NAN;
+  w->nleg = 4 + ng;
+  w->g = sqrt(4.0 * PI_R * o->alpha_s);
+  w->mt = o->mt;
+  w->wt = o->wt;
+  for (int mu = 0; mu < 4; mu++) {
+    w->kin[0][mu] = mom[mu];
+    w->kin[1][mu] = mom[4 + mu];
+    w->kin[2][mu] = -mom[8 + mu];
+    w->kin[3][mu] = -mom[12 + mu];
+    for (int i = 0; i < ng; i++) w->kin[4 + i][mu] = -mom[16 + 4 * i + mu];
+  }
+  real pol[2][2][4];
+  for (int i = 0; i < ng; i++) {
+    polarisation(mom + 16 + 4 * i, 0, pol[i][0]);
+    polarisation(mom + 16 + 4 * i, 1, pol[i][1]);
+  }
+  real sum = 0.0;
+  const int npol = eps_in ? 1 : (1 << ng);
+  for (int s = 0; s < 16; s++) {
+    cplx v2[4], u3[4];
+    spinor_u(mom, 0.0, s & 1, w->u1);
+    spinor_v(mom + 4, 0.0, (s >> 1) & 1, v2);
+    dirac_bar(v2, w->vb2);
+    spinor_u(mom + 8, o->mt, (s >> 2) & 1, u3);
+    dirac_bar(u3, w->ub3);
+    spinor_v(mom + 12, o->mt, (s >> 3) & 1, w->v4);
+    for (int h = 0; h < npol; h++) {
+      for (int i = 0; i < ng; i++)
+        for (int mu = 0; mu < 4; mu++)
+          w->eps[4 + i][mu] = eps_in ? eps_in[4 * i + mu] : (cplx)pol[i][(h >> i) & 1][mu];
+      sum += qq_colour_sum(w);
+    }
+  }
+  free(w);
+  if (eps_in) return sum;
+  real iden = 36.0;
+  for (int i = 2; i <= ng; i++) iden *= i;
+  return sum / iden;
+}
+
+/* Test hook: |M|^2 summed over quark spins and all colours for given complex
+ * gluon polarisations eps[ng][4] (interleaved re, im); eps = k gives the Ward
+ * identity. */
+int mgo_uutt_ng_fixed_pol(int ng, const double* params, const double* mom, const double* eps, double* out) {
+  if (ng < 1 || ng > 2) return MGO_ERR_ARG;
+  oparams o;
+  unpack_params(params, &o);
+  real p[4 * QQ_LEGS];
+  for (int i = 0; i < 4 * (4 + ng); i++) p[i] = mom[i];
+  cplx e[2 * 4];
+  for (int i = 0; i < 4 * ng; i++) e[i] = eps[2 * i] + I * eps[2 * i + 1];
+  *out = (double)me_uutt_ng(&o, ng, p, e);
+  return MGO_OK;
+}
+
+/* Test hook: the two-line recursion for 0, 1 or 2 gluons (the 0- and 1-gluon
+ * cases are evaluated independently by me_uutt and me_uuttg). */
+int mgo_uutt_ng(int ng, const double* params, const double* mom, int64_t nevt, double* me) {
+  if (ng < 0 || ng > 2 || nevt < 0) return MGO_ERR_ARG;
+  oparams o;
+  unpack_params(params, &o);
+  const int npar = 4 + ng;
+  for (int64_t e = 0; e < nevt; e++) {
+    real p[4 * QQ_LEGS];
+    for (int i = 0; i < 4 * npar; i++) p[i] = mom[(size_t)e * npar * 4 + i];
+    me[e] = (double)me_uutt_ng(&o, ng, p, NULL);
+  }
+  return MGO_OK;
+}
+
 /* g(p1) g(p2) -> t(p3) t~(p4) g(p5) ... : n gluons in total.
  * flow_w (may be NULL): sum over spin states of |A(sigma)|^2 per ordering. */
 static real me_ggtt_ng_w(const oparams* o, int n, const real* mom, real* flow_w);
@@ -1162,6 +1564,7 @@ static int proc_gluons(int proc) {
 int mgo_npar(int proc) {
   if (proc == MGO_EEMUMU || proc == MGO_UUTT) return 4;
   if (proc == MGO_UUTTG) return 5;
+  if (proc == MGO_UUTTGG) return 6;
   const int n = proc_gluons(proc);
   return n ? n + 2 : MGO_ERR_ARG;
 }
@@ -1198,7 +1601,8 @@ int mgo_me(int proc, const double* params, const double* mom, int64_t nevt, doub
     me[e] = (double)((proc == MGO_EEMUMU) ? me_eemumu(&o, p)
                      : (proc == MGO_UUTT) ? me_uutt(&o, p)
                      : (proc == MGO_UUTTG) ? me_uuttg(&o, p)
-                                          : me_ggtt_ng(&o, proc_gluons(proc), p));
+                     : (proc == MGO_UUTTGG) ? me_uutt_ng(&o, 2, p, NULL)
+                                           : me_ggtt_ng(&o, proc_gluons(proc), p));
   }
   return MGO_OK;
 }

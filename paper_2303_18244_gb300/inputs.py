@@ -161,6 +161,7 @@ PROCESS_FINAL_MASSES = {
     "g g > t t~ g g g": ("mt", "mt", 0.0, 0.0, 0.0),
     "u u~ > t t~": ("mt", "mt"),
     "u u~ > t t~ g": ("mt", "mt", 0.0),
+    "u u~ > t t~ g g": ("mt", "mt", 0.0, 0.0),
 }
 
 

@@ -64,6 +64,17 @@ MUTANTS = [
     ("a gluon's polarisation state read from its neighbour's helicity bit",
      "q.eps[i][mu] = pol[i][(h >> i) & 1][mu];", "q.eps[i][mu] = pol[i][(h >> (i + 1)) & 1][mu];",
      lambda: P.test_spin_colour_summed_me_and_normalisation(3, 61)),
+    ("two-line recursion: four-gluon term with the wrong sign",
+     "acc[c][x][mu] += -g * g * lor; /* (-i/P^2) (-i g^2) */", "acc[c][x][mu] += g * g * lor;",
+     lambda: P.test_uuttgg_ward_identity(0)),
+    ("two-line recursion: light-quark propagator with the attached momenta reversed",
+     "Q[mu] = (kind == 4) ? (kend[mu] + attached) : (-kend[mu] - attached);",
+     "Q[mu] = (kind == 4) ? (kend[mu] + attached) : (-kend[mu] + attached);",
+     P.test_two_line_recursion_reproduces_uutt_and_uuttg),
+    ("two-line recursion: top line closed with the colour generator transposed",
+     "if (tc != 0) acc[c][x][mu] += g * tc * rv; /* (-i/P^2) (i g) */",
+     "if (tc != 0) acc[c][x][mu] += g * TGEN[c][n][m] * rv;",
+     P.test_two_line_recursion_reproduces_uutt_and_uuttg),
 ]
 
 

@@ -535,3 +535,66 @@ def test_spin_colour_summed_me_and_normalisation(n, seed):
     iden = 2 * 2 * O.generators().shape[0] ** 2 * sym
     assert iden == {3: 256, 4: 512, 5: 1536}[n]  # the normalisation of the matrix element definition
     assert abs(total / iden / O.me(proc, p[None])[0] - 1) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# u u~ -> t t~ g g: colour-dressed recursion over both quark lines
+# --------------------------------------------------------------------------
+
+def test_two_line_recursion_reproduces_uutt_and_uuttg():
+    """The same recursion with no gluon and with one gluon gives the
+    independently pinned u u~ -> t t~ (analytic LO result) and u u~ -> t t~ g
+    (five explicit diagrams, Ward identity) values: the quark lines, their
+    propagators, the closing of the top line into a gluon and the three-gluon
+    vertex on the s-channel gluon are those of the tested evaluations."""
+    p0 = process_momenta("u u~ > t t~", 1000.0, 12, 71)
+    np.testing.assert_allclose(O.uutt_ng(0, p0), O.me("u u~ > t t~", p0), rtol=1e-13)
+    p1 = process_momenta("u u~ > t t~ g", 1200.0, 4, 72)
+    np.testing.assert_allclose(O.uutt_ng(1, p1), O.me("u u~ > t t~ g", p1), rtol=1e-12)
+
+
+@pytest.mark.parametrize("ev", [0, 1])
+def test_uuttgg_ward_identity(ev):
+    """eps_i -> k_i of either gluon annihilates the colour-dressed amplitude,
+    summed over every colour and quark spin (Gamma_t = 0): fixes the
+    four-gluon vertex and the two-gluon currents relative to the rest."""
+    par = O.Params(wt=0.0)
+    p = process_momenta("u u~ > t t~ g g", 1500.0, 2, 73)[ev]
+    e5 = (O.polarisation(p[4], 0) + 0.3j * O.polarisation(p[4], 1)).astype(complex)
+    e6 = (O.polarisation(p[5], 1) - 0.7j * O.polarisation(p[5], 0)).astype(complex)
+    ref = O.uutt_ng_fixed_pol(2, p, [e5, e6], par)
+    assert ref > 0
+    w5 = O.uutt_ng_fixed_pol(2, p, [p[4].astype(complex), e6], par)
+    w6 = O.uutt_ng_fixed_pol(2, p, [e5, p[5].astype(complex)], par)
+    # |M|^2 is quadratic in the amplitude: 1e-11 of it at the amplitude level
+    assert w5 <= 1e-22 * ref * p[4, 0] ** 2
+    assert w6 <= 1e-22 * ref * p[5, 0] ** 2
+
+
+def test_uuttgg_bose_symmetry_and_lorentz_invariance():
+    par = O.Params(wt=0.0)
+    p = process_momenta("u u~ > t t~ g g", 1500.0, 2, 74)
+    me = O.me("u u~ > t t~ g g", p)
+    q = p.copy()
+    q[:, [4, 5]] = q[:, [5, 4]]
+    np.testing.assert_allclose(O.me("u u~ > t t~ g g", q), me, rtol=1e-12)
+    me0 = O.me("u u~ > t t~ g g", p, par)
+    r = _boost_rotate(p, [0.3, -0.2, 0.5], [1, 2, 3], 0.7)
+    np.testing.assert_allclose(O.me("u u~ > t t~ g g", r, par), me0, rtol=1e-11)
+
+
+def test_uuttgg_gluon_spin_sum_and_normalisation():
+    """The ME rebuilt from the fixed-polarisation hook: the gluon spins summed
+    over circular polarisations built here (a basis other than the oracle's
+    linear one), divided by 2*2 initial quark spins, 3*3 initial colours and
+    the final-state symmetry factor counted from Bose symmetry (2 for two
+    gluons): 72."""
+    proc = "u u~ > t t~ g g"
+    p = process_momenta(proc, 1500.0, 1, 75)[0]
+    pols = [_circular_polarisations(p[s], outgoing=True) for s in (4, 5)]
+    total = sum(O.uutt_ng_fixed_pol(2, p, [pols[0][a], pols[1][b]]) for a in range(2) for b in range(2))
+    sym = _final_gluon_symmetry(proc, p, 4)
+    assert sym == 2
+    iden = 2 * 2 * 3 * 3 * sym
+    assert iden == 72
+    assert abs(total / iden / O.me(proc, p[None])[0] - 1) < 1e-12
