@@ -50,6 +50,7 @@ WORKLOADS = {
     "ggttggg": ("g g > t t~ g g g", 2000.0, 4, 65536),
     "uutt": ("u u~ > t t~", 1000.0, 7, 524288),
     "uuttg": ("u u~ > t t~ g", 1200.0, 8, 524288),
+    "uuttgg": ("u u~ > t t~ g g", 1500.0, 9, 524288),
 }
 METRIC = "gg→tt̄gg MEs/s on 1 GB300, FP64 vs mixed (≤1e-5 rel err); serve p50/p99 ms"
 L2_FLUSH_BYTES = 256 << 20
@@ -492,7 +493,7 @@ def main():
         res["accuracy_vs_oracle"] = acc
     if not args.no_configs and args.proc == "ggttgg" and world == 1:  # one GPU: the set's other workloads
         res["configs"] = {t: measure_config(t, mg, process_momenta, timed_call, peak32, peak64)
-                          for t in ("eemumu", "ggtt", "ggttggg")}
+                          for t in ("eemumu", "ggtt", "ggttggg", "uuttgg")}
     if not args.no_serve and args.proc == "ggttgg":
         nreq = args.serve_requests or (2000 if args.serve else 1000)
         plan = {"mixed": nreq, "fp64": max(1, nreq // 5)}

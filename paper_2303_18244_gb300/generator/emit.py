@@ -30,6 +30,7 @@ PROCESSES = {
     "e+ e- > mu+ mu-": ("eemumu", 0),
     "u u~ > t t~": ("uutt", 0),
     "u u~ > t t~ g": ("uuttg", 0),
+    "u u~ > t t~ g g": ("uuttgg", 0),
     "g g > t t~": ("ggtt", 2),
     "g g > t t~ g": ("ggttg", 3),
     "g g > t t~ g g": ("ggttgg", 4),
@@ -1132,6 +1133,9 @@ def emit(proc: str, prec: str = "f64") -> tuple[str, str]:
         src = emit_uutt(tag)
     elif tag == "uuttg":
         src = emit_uuttg(tag)
+    elif tag == "uuttgg":
+        from .two_lines import emit_uuttgg
+        src = emit_uuttgg(tag)
     else:
         src = emit_gg(n, tag, mode="chunked" if tag in CHUNKED else "straight", chunk_order=chunk_order(prec))
     src = _prepare_in_D(src)
@@ -1184,6 +1188,7 @@ THREADS = {
     "eemumu": (128, 128),
     "uutt": (128, 128),
     "uuttg": (128, 128),
+    "uuttgg": (64, 128),
     "ggtt": (128, 128),
     "ggttg": (128, 128),
     "ggttgg": (64, 128),
@@ -1217,7 +1222,7 @@ VERTEX_CALLS = {"f32": {"ggttgg", "ggttggg"}, "f64": set()}
 
 
 # colour-flow counts of the processes written by hand (gg processes: n!)
-FIXED_NCOL = {"eemumu": 1, "uutt": 1, "uuttg": 4}
+FIXED_NCOL = {"eemumu": 1, "uutt": 1, "uuttg": 4, "uuttgg": 12}
 
 
 def emit_tu(proc: str, prec: str) -> tuple[str, str]:

@@ -18,6 +18,7 @@ MIXED_BOUNDS = {
     "g g > t t~ g g g": (6e-6, 2e-5, 1e-3),   # measured 5.5e-7 / 1.3e-6 / 1.1e-4
     "u u~ > t t~": (2e-6, 5e-6, 1e-5),        # measured 1.4e-7 / 4.7e-7 / 8.2e-7
     "u u~ > t t~ g": (2e-6, 6e-6, 3e-5),      # measured 1.4e-7 / 5.5e-7 / 2.4e-6
+    "u u~ > t t~ g g": (3e-6, 1e-5, 3e-4),    # not yet measured on a full workload: the gg -> t t~ g g bounds
 }
 
 

@@ -70,6 +70,7 @@ CASES = {
     "g g > t t~ g g g": (2000.0, 2),
     "u u~ > t t~": (1000.0, 50),
     "u u~ > t t~ g": (1200.0, 20),
+    "u u~ > t t~ g g": (1500.0, 6),
 }
 
 

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 CASES = [("e+ e- > mu+ mu-", 500.0, 1), ("g g > t t~", 1000.0, 2), ("g g > t t~ g", 1200.0, 6),
          ("g g > t t~ g g", 1500.0, 3), ("g g > t t~ g g g", 2000.0, 4), ("u u~ > t t~", 1000.0, 7),
-         ("u u~ > t t~ g", 1200.0, 8)]
+         ("u u~ > t t~ g", 1200.0, 8), ("u u~ > t t~ g g", 1500.0, 9)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -21,7 +21,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("proc,sqrts,seed", CASES, ids=["eemumu", "ggtt", "ggttg", "ggttgg", "ggttggg", "uutt", "uuttg"])
+@pytest.mark.parametrize("proc,sqrts,seed", CASES, ids=["eemumu", "ggtt", "ggttg", "ggttgg", "ggttggg", "uutt", "uuttg", "uuttgg"])
 def test_device_stream_matches_host(proc, sqrts, seed):
     h = mg.Process(proc)
     n, first = 5000, 123456
