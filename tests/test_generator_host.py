@@ -79,3 +79,80 @@ def test_amplitude_terms_and_header_constants(proc, n):
     gluons = frozenset(range(n))
     assert int(const["NDIAG"]) == _line(gluons, 1)
     assert int(const["NAMP"]) == _line(gluons, 3)
+
+
+# u u~ -> t t~ + gluons: the top line as one leaf "T" of the gluon trees on
+# the light line.  The top line carries an ordered sequence of gluon currents
+# over its own gluons plus the gluon joining it to the rest, which sits at any
+# of the m + 1 places around m attached currents.
+def _top(gs, quartic_weight):
+    if not gs:
+        return 1
+    tot = 0
+    items = sorted(gs)
+    for r in range(1, len(items) + 1):
+        for first in combinations(items, r):
+            f = frozenset(first)
+            rest = gs - f
+            # sequences starting with block f; weight (m + 1) summed over the tail
+            tot += _currents(f, quartic_weight) * _top_tail(rest, quartic_weight, 1)
+    return tot
+
+
+def _top_tail(gs, quartic_weight, m):
+    """sum over ordered sequences of blocks covering gs, after m blocks, of
+    (m + blocks + 1) * product of current counts."""
+    if not gs:
+        return m + 1
+    tot = 0
+    items = sorted(gs)
+    for r in range(1, len(items) + 1):
+        for first in combinations(items, r):
+            f = frozenset(first)
+            tot += _currents(f, quartic_weight) * _top_tail(gs - f, quartic_weight, m + 1)
+    return tot
+
+
+def _two_lines(ngluons, quartic_weight):
+    gluons = frozenset(f"g{i}" for i in range(ngluons))
+    tot = 0
+    for r in range(len(gluons) + 1):
+        for gt in combinations(sorted(gluons), r):
+            tot += _top(frozenset(gt), quartic_weight) * _line((gluons - frozenset(gt)) | {"T"}, quartic_weight)
+    return tot
+
+
+def test_two_line_diagram_counts():
+    """u u~ -> t t~ + 0, 1, 2 gluons: 1, 5 and 36 Feynman diagrams (38 terms
+    with the four-gluon vertex split into its colour structures), from the
+    recursion above and from the generator's enumeration rooted at the u."""
+    from paper_2303_18244_gb300.generator import two_lines
+    assert [_two_lines(n, 1) for n in range(3)] == [1, 5, 36]
+    assert _two_lines(2, 3) == 38
+    assert two_lines.count_feynman_diagrams() == 36 and len(two_lines.diagrams()) == 38
+    tag, src = emit.emit("u u~ > t t~ g g")
+    assert "static constexpr int NDIAG = 36;" in src and "static constexpr int NAMP = 38;" in src
+
+
+def test_two_line_colour_flows():
+    """The twelve colour flows of u u~ -> t t~ g g are independent, every
+    diagram term decomposes onto them exactly (checked inside), and the colour
+    matrix has the entries derived by hand from Tr(T^a T^b) = delta/2 and the
+    Fierz identity: 16 on the diagonal (N C_F^2 N or (N C_F)^2), -2 between
+    the two orders of the gluons on one chain (N C_F (C_F - N/2) N), 16/3
+    between the pairings for the same generator string (N C_F^2), 0 between
+    a two-gluon chain and a split in the same pairing."""
+    from fractions import Fraction
+
+    from paper_2303_18244_gb300.generator import two_lines
+    names = [n for n, _ in two_lines.basis()]
+    C = two_lines.colour_matrix()
+    assert len(two_lines.decomposition()) == 38
+    idx = {n: i for i, n in enumerate(names)}
+    for i in range(12):
+        assert C[i][i] == 16
+        for j in range(12):
+            assert C[i][j] == C[j][i]
+    assert C[idx["ki_jl:ab|1"]][idx["ki_jl:ba|1"]] == -2
+    assert C[idx["ki_jl:ab|1"]][idx["ji_kl:ab|1"]] == Fraction(16, 3)
+    assert C[idx["ki_jl:ab|1"]][idx["ki_jl:a|b"]] == 0
