@@ -497,7 +497,7 @@ def main():
     if not args.no_serve and args.proc == "ggttgg":
         nreq = args.serve_requests or (2000 if args.serve else 1000)
         plan = {"mixed": nreq, "fp64": max(1, nreq // 5)}
-        paced = {"mixed": max(1, nreq // 2), "fp64": max(1, nreq // 4)}
+        paced = {"mixed": max(1, nreq // 2), "fp64": max(1, nreq // 20)}
         res["serve"] = serve_bench(plan, mg, process_momenta, paced)
     if rank == 0:
         print(json.dumps(res))

@@ -64,3 +64,35 @@ def test_rejects_sizes_beyond_the_array():
     # the largest accepted size works
     n, mask = mg.good_helicities_static(h, p[:nmax])
     assert 1 <= n <= 64 and mask.sum() == n
+
+
+def test_largest_helicity_count_at_the_size_limit():
+    """g g > t t~ g g g has MG_STATIC_MAX_HEL = 128 helicities: 8191 events
+    fill the array up to its reduction slots and match the allocating filter;
+    8192 events are refused with MG_ERR_ARG before anything runs."""
+    proc = "g g > t t~ g g g"
+    nmax = (SCRATCH_DOUBLES - MAX_HEL) // MAX_HEL
+    assert nmax == 8191
+    p = _dev(process_momenta(proc, 2000.0, nmax + 1, 1004))
+    h_alloc = mg.Process(proc)
+    h_static = mg.Process(proc)
+    assert mg.lib().mg_good_helicities_static(h_static.handle, p.data_ptr(), nmax + 1, None, None) == -2
+    for _ in range(2):
+        n_a, m_a = mg.good_helicities(h_alloc, p[:nmax])
+        n_s, m_s = mg.good_helicities_static(h_static, p[:nmax])
+        assert n_s == n_a and np.array_equal(m_s, m_a)
+
+
+def test_no_information_keeps_every_helicity():
+    """Calibration events without a positive finite |M|^2 (here NaN momenta,
+    which stay in their own lanes) say nothing about the helicities: both
+    filters keep all of them, and the count equals the mask's sum."""
+    proc = "e+ e- > mu+ mu-"
+    bad = _dev(np.full((64, 4, 4), np.nan))
+    for fn in (mg.good_helicities, mg.good_helicities_static):
+        h = mg.Process(proc)
+        n0, _ = fn(h, _dev(process_momenta(proc, 500.0, 256, 1001)))  # a filtered list first
+        assert n0 == 4
+        n, mask = fn(h, bad)
+        assert n == 16 and mask.sum() == 16
+        assert mg.process_status(h) == 0
