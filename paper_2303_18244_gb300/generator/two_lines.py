@@ -43,7 +43,6 @@ from __future__ import annotations
 
 from fractions import Fraction
 from functools import lru_cache
-from itertools import product
 
 import numpy as np
 
@@ -210,7 +209,6 @@ def diagram_colour(d) -> np.ndarray:
 def basis() -> list[tuple[str, np.ndarray]]:
     """The twelve colour flows: (name, tensor [i][j][k][l][a][b])."""
     T, _ = _su3()
-    d = np.eye(3)
 
     def chain(seq):
         m = np.eye(3, dtype=complex)[None, None]  # [a][b][row][col]
@@ -231,7 +229,6 @@ def basis() -> list[tuple[str, np.ndarray]]:
             else:                    # (..)_{j i} (..)_{k l}
                 t = np.einsum("abji,abkl->ijklab", c1, c2)
             out.append((f"{pairing}:{s1 or '1'}|{s2 or '1'}", t))
-    del d
     return out
 
 
