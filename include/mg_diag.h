@@ -25,6 +25,15 @@ extern "C" {
  * MG_ERR_ARG or MG_ERR_CUDA (codes of mg.h). */
 int mg_diag_fma_peak(int kind, double* gflops);
 
+/* Dense FP16 tensor-core throughput of the current device, as the colour
+ * kernels use it: one CTA per SM issues 16384 tcgen05.mma kind::f16 of
+ * M = N = 128, K = 16 (FP16 operands in shared memory, FP32 accumulation in
+ * tensor memory) back to back, timed with CUDA events on a private stream
+ * after one shorter warm-up launch.  *tflops receives 2 M N K MMAs / second /
+ * 1e12.  Synchronous.  Returns MG_OK, MG_ERR_ARG, MG_ERR_CUDA or
+ * MG_ERR_TIMEOUT (the bounded wait for the MMAs ran out). */
+int mg_diag_mma_peak(double* tflops);
+
 typedef struct mg_process mg_process;
 
 /* One mg_sigma call (same arguments, same kernels) with CUDA events recorded

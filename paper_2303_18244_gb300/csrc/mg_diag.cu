@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "mg.h"
+#include "mg_colour_tc.cuh"
 #include "mg_diag.h"
 #include "mg_runtime_internal.h"
 
@@ -58,7 +59,93 @@ int run(double* gflops) {
   return MG_OK;
 }
 
+// Tensor-core probe: one CTA per SM, one elected thread issues `iters`
+// tcgen05.mma kind::f16 of M = 128, N = 128, K = 16 (FP16 operands in shared
+// memory, one FP32 accumulator in TMEM) back to back, then commits; every
+// thread waits (bounded) for the commit.  The large dynamic shared-memory
+// request only keeps a second CTA off the SM.
+constexpr int MMA_M = 128, MMA_N = 128, MMA_K = 16;
+constexpr size_t MMA_PROBE_SMEM = 160 * 1024;
+
+__global__ void __launch_bounds__(128) mma_probe(int iters, unsigned* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ __align__(128) unsigned char tiles[(MMA_M + MMA_N) * MMA_K * 2];  // A [M][K], B [N][K] FP16
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x;
+  if (tid == 0) dyn[0] = 0;
+  for (int i = tid; i < (int)(sizeof(tiles) / 4); i += 128)
+    reinterpret_cast<uint32_t*>(tiles)[i] = 0x3c003c00u;  // FP16 1.0 in both halves
+  if (tid == 0) {
+    mg::mbar_init(&bar, 1);
+    mg::fence_mbar_init();
+  }
+  if (tid < 32) {
+    mg::tc::tmem_alloc(&tslot, MMA_N);
+    mg::tc::tmem_relinquish();
+  }
+  mg::fence_proxy_async_smem();
+  mg::tc::fence_before_sync();
+  __syncthreads();
+  mg::tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = mg::tc::idesc_f16(MMA_M, MMA_N);
+    constexpr uint32_t SBO = (MMA_K / 8) * 128;  // 8-row groups of K-major core matrices
+    const uint32_t a = mg::smem_u32(tiles), b = a + MMA_M * MMA_K * 2;
+    const uint64_t ad = mg::tc::smem_desc(a, mg::tc::LBO, SBO), bd = mg::tc::smem_desc(b, mg::tc::LBO, SBO);
+    for (int i = 0; i < iters; i++) mg::tc::mma_f16(tmem, ad, bd, idesc, i > 0 ? 1u : 0u);
+    mg::tc::mma_commit(&bar);
+  }
+  if (!__syncthreads_and(mg::mbar_wait_bounded(&bar, 0, mg::WAIT_POLLS) ? 1 : 0)) {
+    if (tid == 0) atomicOr(status, 1u);
+    mg::mbar_wait_bounded(&bar, 0, mg::WAIT_POLLS);
+  }
+  mg::tc::fence_before_sync();
+  __syncthreads();
+  if (tid < 32) {
+    mg::tc::fence_after_sync();
+    mg::tc::tmem_dealloc(tmem, MMA_N);
+  }
+}
+
 }  // namespace
+
+extern "C" int mg_diag_mma_peak(double* tflops) {
+  if (!tflops) return MG_ERR_ARG;
+  int dev, sms;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MG_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MG_ERR_CUDA;
+  if (cudaFuncSetAttribute(mma_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMA_PROBE_SMEM) !=
+      cudaSuccess)
+    return MG_ERR_CUDA;
+  unsigned* st = nullptr;
+  if (cudaMalloc(&st, sizeof(unsigned)) != cudaSuccess) return MG_ERR_CUDA;
+  cudaStream_t s;
+  cudaEvent_t e0, e1;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemsetAsync(st, 0, sizeof(unsigned), s);
+  const int iters = 16384;
+  mma_probe<<<sms, 128, MMA_PROBE_SMEM, s>>>(iters / 8, st);  // warm-up
+  cudaEventRecord(e0, s);
+  mma_probe<<<sms, 128, MMA_PROBE_SMEM, s>>>(iters, st);
+  cudaEventRecord(e1, s);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  unsigned flag = 0;
+  if (err == cudaSuccess) err = cudaMemcpy(&flag, st, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  cudaFree(st);
+  if (err != cudaSuccess || ms <= 0.f) return MG_ERR_CUDA;
+  if (flag) return MG_ERR_TIMEOUT;
+  *tflops = 2.0 * MMA_M * MMA_N * MMA_K * double(iters) * sms / (ms * 1e-3) / 1e12;
+  return MG_OK;
+}
 
 extern "C" int mg_diag_fma_peak(int kind, double* gflops) {
   if (!gflops) return MG_ERR_ARG;

@@ -34,7 +34,7 @@ EXPORTS = (
     "mg_server_cfg_default", "mg_server_create", "mg_server_submit", "mg_server_poll",
     "mg_server_destroy", "mg_strerror",
     # include/mg_diag.h
-    "mg_diag_fma_peak", "mg_diag_sigma_phases", "mg_diag_set_wait_polls",
+    "mg_diag_fma_peak", "mg_diag_mma_peak", "mg_diag_sigma_phases", "mg_diag_set_wait_polls",
 )
 
 
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
         L.mg_server_destroy.argtypes = [vp]
         L.mg_server_destroy.restype = None
         L.mg_diag_fma_peak.argtypes = [ctypes.c_int, dp]
+        L.mg_diag_mma_peak.argtypes = [dp]
         fp = ctypes.POINTER(ctypes.c_float)
         L.mg_diag_sigma_phases.argtypes = [vp, vp, i64, vp, vp, fp, fp, ip]
         L.mg_diag_set_wait_polls.argtypes = [vp, ctypes.c_uint32]
@@ -357,3 +358,10 @@ DIAG_WAIT_POLLS = 1 << 22
 def diag_set_wait_polls(h: Process, polls: int):
     """Bound of the first wait on each device barrier of h's kernels (include/mg_diag.h)."""
     _check(lib().mg_diag_set_wait_polls(h.handle, polls), "mg_diag_set_wait_polls")
+
+
+def diag_mma_peak() -> float:
+    """Measured dense FP16 tcgen05 MMA throughput in TFLOP/s (include/mg_diag.h)."""
+    t = ctypes.c_double()
+    _check(lib().mg_diag_mma_peak(ctypes.byref(t)), "mg_diag_mma_peak")
+    return t.value
