@@ -152,6 +152,8 @@ def traffic_per_launch(tag: str, nevt: int):
 
 
 def measured_peak(key: str):
+    """A peak measured on this machine's GPUs (copy bandwidth GB/s, BF16 GEMM
+    TFLOP/s), or None."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
@@ -175,16 +177,6 @@ def launches_per_sigma(proc: str, nevt: int, ngood: int) -> int:
     per_hel = 120 * ((nevt + 127) // 128 * 128) * 8
     hs = max(1, min(ngood, (1 << 30) // per_hel))
     return 2 * ((ngood + hs - 1) // hs)
-
-
-def measured_hbm_gbs():
-    """The measured copy bandwidth of this machine's GPUs (GB/s), or None."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            return float(json.load(f)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return None
 
 
 def time_oracle(proc: str, sqrts: float, seed: int, first_event: int, budget_s: float = 12.0,
@@ -408,7 +400,7 @@ def main():
     uwb_ms, uwb_kept = unweight_ms(w_big, r_big)
     del w_big, r_big
     uw_t, uwb_t = max_over_ranks([uw_ms, uwb_ms], device="cuda")
-    hbm_peak = measured_hbm_gbs()
+    hbm_peak = measured_peak("hbm_gbs")
     # algorithmic bytes: w and r read once (16 B per event), 8 B per kept index
     uwb_bytes = 16 * 128 * nevt + 8 * uwb_kept
 
