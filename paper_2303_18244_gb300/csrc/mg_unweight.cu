@@ -15,6 +15,10 @@
 
 #include "mg.h"
 
+#ifndef MG_UW_PREFETCH
+#define MG_UW_PREFETCH 1
+#endif
+
 namespace {
 
 constexpr int UW_THREADS = 256;
@@ -23,10 +27,12 @@ constexpr int UW_TILE = UW_THREADS * UW_PER_THREAD;  // events per tile
 constexpr int UW_WARPS = UW_THREADS / 32;
 constexpr int UW_WORDS = UW_PER_THREAD * UW_WARPS;  // accept-bit words per tile
 
+#if !MG_UW_PREFETCH
 __device__ __forceinline__ bool kept(const double* __restrict__ w, const double* __restrict__ r, double w_max,
                                      long long i) {
   return r[i] * w_max < w[i];
 }
+#endif
 
 // Pass 1.  Thread t of tile b takes events b*TILE + j*THREADS + t, j < PER_THREAD
 // (coalesced); word j*WARPS + warp of the tile's bits holds the ballot of
@@ -39,11 +45,26 @@ __global__ void __launch_bounds__(UW_THREADS)
   const long long base = (long long)blockIdx.x * UW_TILE;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned* tb = bits + (long long)blockIdx.x * UW_WORDS;
+  // every load of the tile issued before the first vote (MG_UW_PREFETCH=0:
+  // loads interleaved with the votes)
+#if MG_UW_PREFETCH
+  double wv[UW_PER_THREAD], rv[UW_PER_THREAD];
+#pragma unroll
+  for (int j = 0; j < UW_PER_THREAD; j++) {
+    const long long i = base + j * UW_THREADS + threadIdx.x;
+    wv[j] = i < n ? __ldcs(w + i) : 0.0;
+    rv[j] = i < n ? __ldcs(r + i) : 1.0;
+  }
+#endif
   int c = 0;
 #pragma unroll
   for (int j = 0; j < UW_PER_THREAD; j++) {
     const long long i = base + j * UW_THREADS + threadIdx.x;
+#if MG_UW_PREFETCH
+    const unsigned m = __ballot_sync(0xffffffffu, i < n && rv[j] * w_max < wv[j]);
+#else
     const unsigned m = __ballot_sync(0xffffffffu, i < n && kept(w, r, w_max, i));
+#endif
     if (lane == 0) tb[j * UW_WARPS + warp] = m;
     c += __popc(m);  // the same in every lane of the warp
   }
