@@ -257,7 +257,12 @@ typedef struct {
 
 int mg_server_cfg_default(mg_server_cfg* cfg);
 
-/* Start the server (one host scheduler thread) on the current device. */
+/* Start the server (one host scheduler thread) on the current device.
+ * While it captures a CUDA graph, a device-wide synchronisation from another
+ * thread (cudaDeviceSynchronize, torch.cuda.synchronize) fails with
+ * cudaErrorStreamCaptureUnsupported; clients that share the device with a
+ * running server synchronise their own streams instead.  The server itself
+ * launches a chunk whose capture failed that way directly. */
 int mg_server_create(const mg_server_cfg* cfg, mg_server** out);
 
 /* Queue a request: nevt events momenta[nevt][npar][4], results written to

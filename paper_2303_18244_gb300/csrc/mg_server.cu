@@ -179,22 +179,34 @@ int mg_server::admit(int si, const Chunk& c) {
     auto it = graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (it == graphs.end()) {
+      // A capture fails when another thread synchronises the whole device
+      // meanwhile (a device-wide wait cannot wait on a capturing stream):
+      // then this chunk is launched directly and the capture is tried again
+      // with the key's next chunk.
       cudaGraph_t g = nullptr;
-      if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MG_ERR_CUDA;
-      const int rc = mg_launch_sigma_locked(h, s.d_mom, c.bucket, s.d_me, s.stream);
-      const cudaError_t e = cudaStreamEndCapture(s.stream, &g);
-      if (rc || e != cudaSuccess) {
+      bool captured = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (captured) {
+        const int rc = mg_launch_sigma_locked(h, s.d_mom, c.bucket, s.d_me, s.stream);
+        const cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+        captured = rc == MG_OK && e == cudaSuccess && g != nullptr &&
+                   cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
-        return MG_ERR_CUDA;
       }
-      const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      if (ei != cudaSuccess) return MG_ERR_CUDA;
-      graphs[key] = exec;
+      if (captured) {
+        graphs[key] = exec;
+      } else {
+        cudaGetLastError();  // the failed capture's error is not the chunk's
+        exec = nullptr;
+      }
     } else {
       exec = it->second;
     }
-    if (cudaGraphLaunch(exec, s.stream) != cudaSuccess) return MG_ERR_CUDA;
+    if (exec) {
+      if (cudaGraphLaunch(exec, s.stream) != cudaSuccess) return MG_ERR_CUDA;
+    } else {
+      const int rc = mg_launch_sigma_locked(h, s.d_mom, c.bucket, s.d_me, s.stream);
+      if (rc) return rc;
+    }
   } else {
     const int rc = mg_launch_sigma(h, s.d_mom, c.bucket, s.d_me, s.stream);
     if (rc) return rc;

@@ -25,10 +25,13 @@ def _cuda():
 
 
 def _alone(h, mom):
+    # the test's own stream only: a device-wide synchronisation is not
+    # permitted while the server thread captures a graph
+    s = torch.cuda.current_stream()
     d = torch.from_numpy(mom).cuda()
     out = torch.empty(mom.shape[0], dtype=torch.float64, device="cuda")
-    mg.sigma(h, d, out)
-    torch.cuda.synchronize()
+    mg.sigma(h, d, out, s)
+    s.synchronize()
     return out.cpu().numpy()
 
 
