@@ -351,6 +351,13 @@ inline bool colour_tile_host(const int* knum, int ncol, unsigned short* out /* [
 // colour_rows_tc_kernel contracts them with the colour matrix on the tensor
 // cores, batched over events x helicities, and sums the helicities per event.
 // ---------------------------------------------------------------------------
+// MG_ROWS_REGS (default 1): the colour kernel holds each row's flows in
+// registers for the helicity (see colour_rows_tc_kernel); 0 reads them from
+// the workspace where they are used.
+#ifndef MG_ROWS_REGS
+#define MG_ROWS_REGS 1
+#endif
+constexpr int ROWS_REGS = MG_ROWS_REGS;  // for the unroll counts (pragmas see no macros)
 template <class P>
 struct LayoutRows {
   static constexpr int K = tc::pad16(P::NCOL);
@@ -414,23 +421,34 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll 1
   for (int ih = 0; ih < nhel && ok; ih++) {
     const float2* row = J + (long long)ih * P::NCOL * ldj + e;
+#if MG_ROWS_REGS
+    // the row's flows into registers with every load in flight at once (one
+    // read of the workspace; the loads of a loop that used each value at
+    // once kept only a few per thread in flight)
+    float2 fv[P::NCOL];
+#pragma unroll
+    for (int k = 0; k < P::NCOL; k++) fv[k] = valid ? __ldcs(row + (long long)k * ldj) : make_float2(0.f, 0.f);
+#define MG_ROW_FLOW(k) fv[k]
+#else
+#define MG_ROW_FLOW(k) row[(long long)(k) * ldj]
+#endif
     float mx = 0.f;
     if (valid) {
-#pragma unroll 8
+#pragma unroll ROWS_REGS ? P::NCOL : 8
       for (int k = 0; k < P::NCOL; k++) {
-        const float2 v = row[(long long)k * ldj];
+        const float2 v = MG_ROW_FLOW(k);
         mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
       }
     }
     const int ex = mx > 0.f ? ((int)((__float_as_uint(mx) >> 23) & 0xff) - 127) : 0;
     const float s = __uint_as_float((uint32_t)(127 - ex) << 23);  // 2^-ex
-#pragma unroll 1
+#pragma unroll ROWS_REGS ? K / 8 : 1
     for (int j = 0; j < K / 8; j++) {
       __align__(16) __half hr[8], lr[8], hi_[8], li[8];
 #pragma unroll
       for (int q = 0; q < 8; q++) {
         const int k = 8 * j + q;
-        const float2 v = (valid && k < P::NCOL) ? row[(long long)k * ldj] : make_float2(0.f, 0.f);
+        const float2 v = (valid && k < P::NCOL) ? MG_ROW_FLOW(k < P::NCOL ? k : 0) : make_float2(0.f, 0.f);
         const float xr = s * v.x, xi = s * v.y;
         hr[q] = __float2half_rn(xr);
         lr[q] = __float2half_rn(xr - __half2float(hr[q]));
@@ -468,7 +486,7 @@ __global__ void __launch_bounds__(128, 1)
     phase ^= 1u;
     tc::fence_after_sync();
     float dsum = 0.f;
-#pragma unroll 1
+#pragma unroll ROWS_REGS ? N / 16 : 1
     for (int c = 0; c < N; c += 16) {
       float dr[16], di[16];
       tc::tmem_ld16(lane_base + c, dr);
@@ -477,11 +495,12 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
       for (int q = 0; q < 16; q++) {
         const int k = c + q;
-        const float2 v = (valid && k < P::NCOL) ? row[(long long)k * ldj] : make_float2(0.f, 0.f);
+        const float2 v = (valid && k < P::NCOL) ? MG_ROW_FLOW(k < P::NCOL ? k : 0) : make_float2(0.f, 0.f);
         dsum = fmaf(v.x, dr[q], dsum);
         dsum = fmaf(v.y, di[q], dsum);
       }
     }
+#undef MG_ROW_FLOW
     acc += (double)(dsum / s);
     tc::fence_before_sync();
     __syncthreads();  // tiles and accumulators are reused by the next helicity
