@@ -13,8 +13,9 @@ bounded sample are reported beside it, with the other workloads of the set
 (e+e- -> mu+mu-, g g -> t t~, g g -> t t~ g g g: mixed and FP64 throughput,
 each kernel's roofline fraction, accuracy against the oracle) under
 "configs", and a run of the continuous-batching request loop (Poisson
-arrivals, four processes, p50/p99 latency; 1000 mixed and 200 FP64 requests,
---serve: 2000 and 400).
+arrivals, four processes, p50/p99 latency; 2000 mixed and 200 FP64 requests,
+then the first half / quarter of them again at 70 % load; --serve: twice as
+many).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 
@@ -245,7 +246,7 @@ def main():
     ap.add_argument("--nevt", type=int, default=None)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--serve", action="store_true",
-                    help="longer serving benchmark (2000 mixed and 400 FP64 requests instead of 1000 and 200)")
+                    help="longer serving benchmark (4000 mixed and 400 FP64 requests instead of 2000 and 200)")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads of the set")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=None)
@@ -487,9 +488,9 @@ def main():
         res["configs"] = {t: measure_config(t, mg, process_momenta, timed_call, peak32, peak64)
                           for t in ("eemumu", "ggtt", "ggttggg", "uuttgg")}
     if not args.no_serve and args.proc == "ggttgg":
-        nreq = args.serve_requests or (2000 if args.serve else 1000)
-        plan = {"mixed": nreq, "fp64": max(1, nreq // 5)}
-        paced = {"mixed": max(1, nreq // 2), "fp64": max(1, nreq // 20)}
+        nreq = args.serve_requests or (4000 if args.serve else 2000)
+        plan = {"mixed": nreq, "fp64": max(1, nreq // 10)}
+        paced = {"mixed": max(1, nreq // 2), "fp64": max(1, nreq // 40)}
         res["serve"] = serve_bench(plan, mg, process_momenta, paced)
     if rank == 0:
         print(json.dumps(res))
