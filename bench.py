@@ -61,7 +61,7 @@ L2_FLUSH_BYTES = 256 << 20
 # the kernel sources at capture time); scaled to a launch by its events (the
 # traffic is per event: momenta in, |M|^2 out).  Reported as null once the
 # sources differ from the captured ones (kernel_digest()).
-NCU_TRAFFIC = {"ggttgg": (65536, 12811008 + 751872, "16e3fd418ccc9a9e")}
+NCU_TRAFFIC = {"ggttgg": (65536, 12815104 + 745216, "bd63ce2f23a8d439")}
 KERNEL_SOURCES = ("mg_kernels.cuh", "mg_vertices.cuh", "mg_colour_tc.cuh", "mg_flowstore.cuh")
 
 SERVE_PROCS = {  # process -> sqrt(s)
