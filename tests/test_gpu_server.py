@@ -15,7 +15,7 @@ from mixed_bounds import MIXED_BOUNDS  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 PROCS = {"e+ e- > mu+ mu-": 500.0, "g g > t t~": 1000.0, "g g > t t~ g": 1200.0, "g g > t t~ g g": 1500.0,
-         "g g > t t~ g g g": 2000.0}
+         "g g > t t~ g g g": 2000.0, "u u~ > t t~ g g": 1500.0}
 
 
 @pytest.fixture(scope="module", autouse=True)
