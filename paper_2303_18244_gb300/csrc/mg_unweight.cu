@@ -15,8 +15,13 @@
 
 #include "mg.h"
 
-#ifndef MG_UW_PREFETCH
-#define MG_UW_PREFETCH 1
+// MG_UW_FP32_FIRST (default 1): the decision r_i * w_max < w_i is taken in
+// FP32 where the FP32 values are far enough apart to make it certain, in FP64
+// otherwise (the FP64 multiply-and-compare of every event made the count pass
+// FP64-bound: 82 % of the FP64 pipe on GB300, where FP64 runs at 1/64 of
+// FP32); the kept set is the same bit for bit.
+#ifndef MG_UW_FP32_FIRST
+#define MG_UW_FP32_FIRST 1
 #endif
 
 namespace {
@@ -27,12 +32,36 @@ constexpr int UW_TILE = UW_THREADS * UW_PER_THREAD;  // events per tile
 constexpr int UW_WARPS = UW_THREADS / 32;
 constexpr int UW_WORDS = UW_PER_THREAD * UW_WARPS;  // accept-bit words per tile
 
-#if !MG_UW_PREFETCH
-__device__ __forceinline__ bool kept(const double* __restrict__ w, const double* __restrict__ r, double w_max,
-                                     long long i) {
-  return r[i] * w_max < w[i];
+// x truncated toward zero to a normal FP32 value, built from its bits with
+// integer operations (no FP64 instruction); false where x is zero, subnormal
+// in FP32, beyond the FP32 range, infinite or NaN.  |x - f| < 2^-23 |x|.
+__device__ __forceinline__ bool f32_trunc(double x, float& f) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);  // biased FP64 exponent
+  if (e < 897 || e > 1150) return false;    // FP32 exponents 1..254
+  f = __uint_as_float((unsigned)(b >> 32 & 0x80000000u) | ((unsigned)(e - 896) << 23) |
+                      (unsigned)((b >> 29) & 0x7fffffu));
+  return true;
 }
+
+// r * w_max < w, exactly as in FP64.  In FP32, p = rf * wmf carries a
+// relative error below 3e-7 from the truncations and the product, and wf
+// below 1.2e-7; a gap |p - wf| above 1e-6 |wf| (with p a normal FP32 value)
+// therefore has the sign of r * w_max - w, which the FP64 product's rounding
+// (1.1e-16) cannot change.  Closer cases, and anything outside the FP32
+// normal range (zero, NaN, infinities included), take the FP64 comparison.
+__device__ __forceinline__ bool kept_exact(double r, double w, double w_max, float wmf, bool wm_ok) {
+#if MG_UW_FP32_FIRST
+  float rf, wf;
+  if (wm_ok && f32_trunc(r, rf) && f32_trunc(w, wf)) {
+    const float p = rf * wmf;
+    const float ap = fabsf(p);
+    const float d = p - wf;
+    if (ap >= 1.17549435e-38f && ap <= 3.40282347e38f && fabsf(d) > 1e-6f * fabsf(wf)) return d < 0.f;
+  }
 #endif
+  return r * w_max < w;
+}
 
 // Pass 1.  Thread t of tile b takes events b*TILE + j*THREADS + t, j < PER_THREAD
 // (coalesced); word j*WARPS + warp of the tile's bits holds the ballot of
@@ -45,9 +74,9 @@ __global__ void __launch_bounds__(UW_THREADS)
   const long long base = (long long)blockIdx.x * UW_TILE;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned* tb = bits + (long long)blockIdx.x * UW_WORDS;
-  // every load of the tile issued before the first vote (MG_UW_PREFETCH=0:
-  // loads interleaved with the votes)
-#if MG_UW_PREFETCH
+  float wmf = 0.f;
+  const bool wm_ok = f32_trunc(w_max, wmf);
+  // every load of the tile issued before the first vote
   double wv[UW_PER_THREAD], rv[UW_PER_THREAD];
 #pragma unroll
   for (int j = 0; j < UW_PER_THREAD; j++) {
@@ -55,16 +84,11 @@ __global__ void __launch_bounds__(UW_THREADS)
     wv[j] = i < n ? __ldcs(w + i) : 0.0;
     rv[j] = i < n ? __ldcs(r + i) : 1.0;
   }
-#endif
   int c = 0;
 #pragma unroll
   for (int j = 0; j < UW_PER_THREAD; j++) {
     const long long i = base + j * UW_THREADS + threadIdx.x;
-#if MG_UW_PREFETCH
-    const unsigned m = __ballot_sync(0xffffffffu, i < n && rv[j] * w_max < wv[j]);
-#else
-    const unsigned m = __ballot_sync(0xffffffffu, i < n && kept(w, r, w_max, i));
-#endif
+    const unsigned m = __ballot_sync(0xffffffffu, i < n && kept_exact(rv[j], wv[j], w_max, wmf, wm_ok));
     if (lane == 0) tb[j * UW_WARPS + warp] = m;
     c += __popc(m);  // the same in every lane of the warp
   }

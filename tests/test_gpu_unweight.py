@@ -90,3 +90,27 @@ def test_unweighted_events_from_matrix_elements():
     # efficiency <w>/w_max within 5 sigma
     p = me.cpu().numpy() / w_max
     assert abs(k - p.sum()) < 5 * np.sqrt((p * (1 - p)).sum())
+
+
+@pytest.mark.parametrize("w_max", [1.7, 3e38, 1e39, 2e-38])
+def test_decisions_at_the_rounding_edge_and_outside_fp32(w_max):
+    """Weights exactly at the FP64 product r * w_max and one ulp on either
+    side (decided by the last bit: the FP64 comparison), and values outside
+    the FP32 normal range (0, FP32-subnormal, beyond FP32, infinite, NaN,
+    negative; w_max itself beyond FP32 or near its bottom): the kept set
+    equals the oracle's definition bit for bit."""
+    rng = np.random.default_rng(5)
+    n = 3 * TILE + 17
+    r = rng.random(n)
+    p = r * w_max
+    k3 = np.arange(n) % 3
+    w = np.where(k3 == 0, p, np.where(k3 == 1, np.nextafter(p, np.inf), np.nextafter(p, -np.inf)))
+    # far from the edge too: decided in FP32
+    w[10::11] = p[10::11] * (1 + 1e-5 * (1 - 2 * (np.arange(10, n, 11) % 2)))
+    for off, v in enumerate((0.0, 1e-40, 1e39, np.inf, np.nan, -1.0, 5e-39, -0.0)):
+        w[off::97] = v
+    r[8::97] = 0.0
+    got, k, _ = _run(w, r, w_max)
+    want = O.unweight(w, r, w_max)
+    assert k == want.size and np.array_equal(got, want)
+    assert 0 < k < n
