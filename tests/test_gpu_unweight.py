@@ -114,3 +114,23 @@ def test_decisions_at_the_rounding_edge_and_outside_fp32(w_max):
     want = O.unweight(w, r, w_max)
     assert k == want.size and np.array_equal(got, want)
     assert 0 < k < n
+
+
+def test_unaligned_inputs_match():
+    """w and r starting 8 bytes past a 16-byte boundary (views one element
+    into their buffers) take the 8-byte loads; odd lengths end on a half
+    pair.  The kept set equals the oracle's either way."""
+    for n in (TILE + 1, 5 * TILE + 333):
+        u = uniforms(23, 0, n + 1, 1)[:, 0, :]
+        w = 4.0 * u[:, 0] ** 2
+        r = u[:, 1]
+        wd = torch.from_numpy(w).cuda()[1:]
+        rd = torch.from_numpy(r).cuda()[1:]
+        assert wd.data_ptr() % 16 == 8
+        idx = torch.full((n,), -7, dtype=torch.int64, device="cuda")
+        cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+        mg.unweight(wd, rd, 1.5, idx, cnt)
+        torch.cuda.synchronize()
+        k = int(cnt.item())
+        want = O.unweight(w[1:], r[1:], 1.5)
+        assert k == want.size and np.array_equal(idx.cpu().numpy()[:k], want)
