@@ -213,8 +213,8 @@ int mg_rambo(const mg_process* h, double sqrt_s, uint64_t seed, int64_t first_ev
  * w_i > w_max are kept (the caller may give them weight w_i / w_max).  Writes
  * the kept indices in increasing order to idx_out_dev (capacity n) and their
  * number to *n_acc_dev (device memory).  Stream-ordered; a workspace of
- * about n / 8 + n / 256 bytes (one accept bit per event and one count per
- * 2048 events) is taken from the stream-ordered allocator (cudaMallocAsync)
+ * about n / 8 + n / 512 bytes (one accept bit per event and one count per
+ * 4096 events) is taken from the stream-ordered allocator (cudaMallocAsync)
  * and released on the same stream.  Errors: MG_ERR_ARG (n < 0, w_max <= 0 or NaN,
  * NULL), MG_ERR_NOMEM, MG_ERR_CUDA. */
 int mg_unweight(const double* w_dev, const double* r_dev, int64_t n, double w_max, int64_t* idx_out_dev,

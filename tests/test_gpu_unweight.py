@@ -11,7 +11,7 @@ from paper_2303_18244_gb300.inputs import process_momenta, uniforms  # noqa: E40
 
 pytestmark = pytest.mark.gpu
 
-TILE = 2048  # events per tile of the device kernels
+TILE = 4096  # events per tile of the device kernels (256 threads x 16)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -32,7 +32,7 @@ def _run(w, r, w_max):
     return idx.cpu().numpy()[:k], k, idx.cpu().numpy()
 
 
-@pytest.mark.parametrize("n", [1, 31, 257, TILE - 1, TILE, TILE + 1, 5 * TILE + 333, 1 << 20, (1 << 23) + 77])
+@pytest.mark.parametrize("n", [1, 31, 257, TILE // 2 + 1, TILE - 1, TILE, TILE + 1, 5 * TILE + 333, 1 << 20, (1 << 23) + 77])
 def test_matches_oracle(n):
     u = uniforms(21, 0, n, 1)[:, 0, :]
     w = 4.0 * u[:, 0] ** 2
