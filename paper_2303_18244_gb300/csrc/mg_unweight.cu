@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "mg.h"
+#include "mg_kernels.cuh"  // mbarrier and bulk-copy primitives
 
 // MG_UW_FP32_FIRST (default 1): the decision r_i * w_max < w_i is taken in
 // FP32 where the FP32 values are far enough apart to make it certain, in FP64
@@ -22,6 +23,12 @@
 // FP32); the kept set is the same bit for bit.
 #ifndef MG_UW_FP32_FIRST
 #define MG_UW_FP32_FIRST 1
+#endif
+// MG_UW_TMA: the count pass takes each full tile of 16-byte aligned w and r
+// into shared memory with two bulk copies (TMA engine) instead of per-thread
+// loads.
+#ifndef MG_UW_TMA
+#define MG_UW_TMA 0
 #endif
 
 namespace {
@@ -96,6 +103,73 @@ __global__ void __launch_bounds__(UW_THREADS)
     const unsigned m = __ballot_sync(0xffffffffu, i < n && kept_exact(rv[j], wv[j], w_max, wmf, wm_ok));
     if (lane == 0) tb[j * UW_WARPS + warp] = m;
     c += __popc(m);  // the same in every lane of the warp
+  }
+  if (lane == 0) warp_sum[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int k = 0; k < UW_WARPS; k++) t += warp_sum[k];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// Pass 1 with the tile staged by the TMA engine: one thread issues two bulk
+// copies (w and r of the tile, 2 x 8 * TILE bytes) that complete on one
+// mbarrier, then every thread reads its events from shared memory; events,
+// bit words and counts as in tile_count_kernel.  Full tiles only, with w and
+// r 16-byte aligned (checked on the host); the partial last tile takes
+// per-thread loads.  A copy that does not complete within the bounded wait
+// is waited for once more (bounded), so that none is left in flight, and the
+// tile is then read from global memory.
+constexpr size_t UW_TMA_SMEM = 128 + 2 * sizeof(double) * UW_TILE;
+
+__global__ void __launch_bounds__(UW_THREADS)
+    tile_count_tma_kernel(const double* __restrict__ w, const double* __restrict__ r, long long n, double w_max,
+                          long long* __restrict__ counts, unsigned* __restrict__ bits) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int warp_sum[UW_WARPS];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  double* sw = reinterpret_cast<double*>(smem + 128);
+  double* sr = sw + UW_TILE;
+  const long long base = (long long)blockIdx.x * UW_TILE;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned* tb = bits + (long long)blockIdx.x * UW_WORDS;
+  float wmf = 0.f;
+  const bool wm_ok = f32_trunc(w_max, wmf);
+  bool staged = false;
+  if (base + UW_TILE <= n) {  // uniform across the CTA
+    if (threadIdx.x == 0) {
+      mg::mbar_init(bar, 1);
+      mg::fence_mbar_init();
+      mg::fence_proxy_async_smem();
+      mg::mbar_arrive_expect_tx(bar, (uint32_t)(2 * sizeof(double) * UW_TILE));
+      mg::bulk_g2s(sw, w + base, (uint32_t)(sizeof(double) * UW_TILE), bar);
+      mg::bulk_g2s(sr, r + base, (uint32_t)(sizeof(double) * UW_TILE), bar);
+    }
+    __syncthreads();
+    staged = __syncthreads_and(mg::mbar_wait_bounded(bar, 0, mg::WAIT_POLLS) ? 1 : 0) != 0;
+    if (!staged) mg::mbar_wait_bounded(bar, 0, mg::WAIT_POLLS);
+  }
+  double wv[UW_PER_THREAD], rv[UW_PER_THREAD];
+#pragma unroll
+  for (int j = 0; j < UW_PER_THREAD; j++) {
+    const int k = j * UW_THREADS + threadIdx.x;
+    const long long i = base + k;
+    if (staged) {
+      wv[j] = sw[k];
+      rv[j] = sr[k];
+    } else {
+      wv[j] = i < n ? __ldcs(w + i) : 0.0;
+      rv[j] = i < n ? __ldcs(r + i) : 1.0;
+    }
+  }
+  int c = 0;
+#pragma unroll
+  for (int j = 0; j < UW_PER_THREAD; j++) {
+    const long long i = base + j * UW_THREADS + threadIdx.x;
+    const unsigned m = __ballot_sync(0xffffffffu, i < n && kept_exact(rv[j], wv[j], w_max, wmf, wm_ok));
+    if (lane == 0) tb[j * UW_WARPS + warp] = m;
+    c += __popc(m);
   }
   if (lane == 0) warp_sum[warp] = c;
   __syncthreads();
@@ -190,7 +264,18 @@ extern "C" int mg_unweight(const double* w_dev, const double* r_dev, int64_t n, 
   const size_t bytes = (size_t)ntiles * (sizeof(long long) + UW_WORDS * sizeof(unsigned));
   if (cudaMallocAsync(reinterpret_cast<void**>(&counts), bytes, s) != cudaSuccess) return MG_ERR_NOMEM;
   unsigned* bits = reinterpret_cast<unsigned*>(counts + ntiles);
-  tile_count_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(w_dev, r_dev, n, w_max, counts, bits);
+  const bool tma = MG_UW_TMA && (reinterpret_cast<uintptr_t>(w_dev) & 15u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(r_dev) & 15u) == 0;
+  if (tma) {
+    if (cudaFuncSetAttribute(tile_count_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)UW_TMA_SMEM) != cudaSuccess) {
+      cudaFreeAsync(counts, s);
+      return MG_ERR_CUDA;
+    }
+    tile_count_tma_kernel<<<(unsigned)ntiles, UW_THREADS, UW_TMA_SMEM, s>>>(w_dev, r_dev, n, w_max, counts, bits);
+  } else {
+    tile_count_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(w_dev, r_dev, n, w_max, counts, bits);
+  }
   tile_scan_kernel<<<1, 1024, 0, s>>>(counts, ntiles, reinterpret_cast<long long*>(n_acc_dev));
   tile_write_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(bits, counts, reinterpret_cast<long long*>(idx_out_dev));
   const cudaError_t e1 = cudaGetLastError();
