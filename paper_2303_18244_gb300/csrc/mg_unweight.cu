@@ -180,33 +180,62 @@ __global__ void __launch_bounds__(UW_THREADS)
   }
 }
 
-// Pass 2: exclusive scan of the tile counts in place (one block: each thread
-// sums a contiguous run of tiles, one block scan of the run sums, each thread
-// rewrites its run); the total into *n_acc.
-__global__ void __launch_bounds__(1024) tile_scan_kernel(long long* __restrict__ counts, long long ntiles,
-                                                         long long* __restrict__ n_acc) {
-  __shared__ long long part[1024];
-  const int t = threadIdx.x;
-  const long long per = (ntiles + 1023) / 1024;
-  const long long b0 = t * per;
-  const long long b1 = b0 + per < ntiles ? b0 + per : ntiles;
-  long long own = 0;
-  for (long long b = b0; b < b1; b++) own += counts[b];
-  part[t] = own;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
-    const long long add = t >= o ? part[t - o] : 0;
+// Pass 2: exclusive scan of the tile counts in place, by one block, in
+// passes of SCAN_T * SCAN_V tiles: thread t of warp w holds the tiles
+// base + j*SCAN_T + t (j < SCAN_V; coalesced loads and stores), so the
+// (j, w, lane) order is the index order.  Warp scans of each j, one scan of
+// the SCAN_V * 32 warp totals in order by the first warp, the pass's total
+// carried to the next; the grand total into *n_acc.
+constexpr int SCAN_T = 1024, SCAN_V = 16, SCAN_W = SCAN_T / 32;
+
+__global__ void __launch_bounds__(SCAN_T) tile_scan_kernel(long long* __restrict__ counts, long long ntiles,
+                                                           long long* __restrict__ n_acc) {
+  __shared__ long long wt[SCAN_V * SCAN_W];  // warp totals, then their exclusive prefixes
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  long long carry = 0;  // kept by the first warp
+  for (long long base = 0; base < ntiles; base += (long long)SCAN_T * SCAN_V) {
+    // tile counts are at most TILE: a warp's partial sums fit in 32 bits
+    int ex[SCAN_V];
+#pragma unroll
+    for (int j = 0; j < SCAN_V; j++) {
+      const long long b = base + (long long)j * SCAN_T + t;
+      ex[j] = b < ntiles ? (int)counts[b] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < SCAN_V; j++) {
+      int x = ex[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += a;
+      }
+      if (lane == 31) wt[j * SCAN_W + warp] = x;
+      ex[j] = x - ex[j];  // exclusive within the warp
+    }
     __syncthreads();
-    part[t] += add;
+    if (warp == 0) {
+#pragma unroll 1
+      for (int q = 0; q < SCAN_V * SCAN_W / 32; q++) {
+        const long long own = wt[q * 32 + lane];
+        long long x = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long a = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += a;
+        }
+        wt[q * 32 + lane] = carry + x - own;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+      }
+    }
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < SCAN_V; j++) {
+      const long long b = base + (long long)j * SCAN_T + t;
+      if (b < ntiles) counts[b] = wt[j * SCAN_W + warp] + ex[j];
+    }
+    __syncthreads();  // wt is rewritten by the next pass
   }
-  long long run = part[t] - own;
-  for (long long b = b0; b < b1; b++) {
-    const long long v = counts[b];
-    counts[b] = run;
-    run += v;
-  }
-  if (t == 1023) *n_acc = part[1023];
+  if (t == 0) *n_acc = carry;
 }
 
 // Pass 3: from the tile's bits only, each kept event's rank in the tile (the
@@ -276,7 +305,7 @@ extern "C" int mg_unweight(const double* w_dev, const double* r_dev, int64_t n, 
   } else {
     tile_count_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(w_dev, r_dev, n, w_max, counts, bits);
   }
-  tile_scan_kernel<<<1, 1024, 0, s>>>(counts, ntiles, reinterpret_cast<long long*>(n_acc_dev));
+  tile_scan_kernel<<<1, SCAN_T, 0, s>>>(counts, ntiles, reinterpret_cast<long long*>(n_acc_dev));
   tile_write_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(bits, counts, reinterpret_cast<long long*>(idx_out_dev));
   const cudaError_t e1 = cudaGetLastError();
   const cudaError_t e2 = cudaFreeAsync(counts, s);

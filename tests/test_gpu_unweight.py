@@ -44,6 +44,22 @@ def test_matches_oracle(n):
     assert np.all(raw[k:n] == -7)  # nothing written past the kept events
 
 
+@pytest.mark.parametrize("n", [16384 * TILE - 3, 16392 * TILE + 5])
+def test_tile_scan_at_67m_events_and_beyond(n):
+    """At 67 M events (16384 tiles: the scan of the tile counts keeps 16 per
+    thread in registers) and past it (17 per thread: batched loads).  Events
+    with w >= w_max are always kept and w <= 0 never, so a kept set chosen in
+    advance, with a pseudo-random density per tile, is the exact answer."""
+    rng = np.random.default_rng(n)
+    tile_p = rng.random(n // TILE + 1) ** 3  # per-tile density, many tiles nearly empty
+    keep = rng.random(n) < np.repeat(tile_p, TILE)[:n]
+    w = np.where(keep, 2.0, 0.0)
+    r = rng.random(n)
+    got, k, _ = _run(w, r, 1.0)
+    want = np.flatnonzero(keep)
+    assert k == want.size and np.array_equal(got, want)
+
+
 def test_all_and_none_kept():
     n = 3 * TILE + 5
     u = uniforms(22, 0, n, 1)[:, 0, 0]
