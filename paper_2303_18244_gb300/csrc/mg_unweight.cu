@@ -240,35 +240,40 @@ __global__ void __launch_bounds__(SCAN_T) tile_scan_kernel(long long* __restrict
 
 // Pass 3: from the tile's bits only, each kept event's rank in the tile (the
 // counts of the words before its word, then the bits below its lane) and its
-// index at the tile's offset.
+// index at the tile's offset.  A tile without kept events (its offset equal
+// to the next tile's, or to the total for the last tile) returns at once.
 __global__ void __launch_bounds__(UW_THREADS)
     tile_write_kernel(const unsigned* __restrict__ bits, const long long* __restrict__ offsets,
-                      long long* __restrict__ idx_out) {
+                      const long long* __restrict__ n_acc, long long* __restrict__ idx_out) {
   constexpr int WPL = UW_WORDS / 32;  // words per lane in the word scan
   static_assert(UW_WORDS % 32 == 0, "whole warps of words");
   __shared__ int word_excl[UW_WORDS];
   const long long base = (long long)blockIdx.x * UW_TILE;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned* tb = bits + (long long)blockIdx.x * UW_WORDS;
+  const long long off = offsets[blockIdx.x];
+  const long long next = blockIdx.x + 1 < gridDim.x ? offsets[blockIdx.x + 1] : *n_acc;
+  if (next == off) return;  // the same for every thread of the tile
   if (warp == 0) {
     // words q*32 + lane in index order: a warp scan per block of 32 words,
     // carried over the blocks
+    int cnt[WPL];
+#pragma unroll
+    for (int q = 0; q < WPL; q++) cnt[q] = __popc(tb[q * 32 + lane]);
     int carry = 0;
 #pragma unroll
     for (int q = 0; q < WPL; q++) {
-      const int cnt = __popc(tb[q * 32 + lane]);
-      int sc = cnt;
+      int sc = cnt[q];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int a = __shfl_up_sync(0xffffffffu, sc, o);
         if (lane >= o) sc += a;
       }
-      word_excl[q * 32 + lane] = carry + sc - cnt;
+      word_excl[q * 32 + lane] = carry + sc - cnt[q];
       carry += __shfl_sync(0xffffffffu, sc, 31);
     }
   }
   __syncthreads();
-  const long long off = offsets[blockIdx.x];
 #pragma unroll
   for (int j = 0; j < UW_PER_THREAD; j++) {
     const int q = j * UW_WARPS + warp;
@@ -306,7 +311,8 @@ extern "C" int mg_unweight(const double* w_dev, const double* r_dev, int64_t n, 
     tile_count_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(w_dev, r_dev, n, w_max, counts, bits);
   }
   tile_scan_kernel<<<1, SCAN_T, 0, s>>>(counts, ntiles, reinterpret_cast<long long*>(n_acc_dev));
-  tile_write_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(bits, counts, reinterpret_cast<long long*>(idx_out_dev));
+  tile_write_kernel<<<(unsigned)ntiles, UW_THREADS, 0, s>>>(bits, counts, reinterpret_cast<long long*>(n_acc_dev),
+                                                            reinterpret_cast<long long*>(idx_out_dev));
   const cudaError_t e1 = cudaGetLastError();
   const cudaError_t e2 = cudaFreeAsync(counts, s);
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? MG_OK : MG_ERR_CUDA;

@@ -60,6 +60,25 @@ def test_tile_scan_at_67m_events_and_beyond(n):
     assert k == want.size and np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("tiles", [(0,), (5,), (0, 5), (2, 3), (1, 4, 5)])
+def test_kept_events_in_some_tiles_only(tiles):
+    """Tiles without kept events are skipped by the write pass (their offset
+    equals the next tile's, or the total for the last one): kept events in
+    chosen tiles only, the last (partial) one included; w >= w_max is always
+    kept and w <= 0 never."""
+    n = 5 * TILE + 333
+    rng = np.random.default_rng(len(tiles))
+    keep = np.zeros(n, dtype=bool)
+    for t in tiles:
+        seg = slice(t * TILE, min(n, (t + 1) * TILE))
+        keep[seg] = rng.random(keep[seg].size) < 0.3
+    w = np.where(keep, 2.0, -1.0)
+    got, k, raw = _run(w, rng.random(n), 1.0)
+    want = np.flatnonzero(keep)
+    assert k == want.size and np.array_equal(got, want)
+    assert np.all(raw[k:n] == -7)
+
+
 def test_all_and_none_kept():
     n = 3 * TILE + 5
     u = uniforms(22, 0, n, 1)[:, 0, 0]
