@@ -1,4 +1,5 @@
-"""Host-side logic of bench.py (no GPU): the oracle's CPU-baseline sample.
+"""Host-side logic of bench.py (no GPU): the oracle's CPU-baseline sample,
+and the reference arm launched on two ranks.
 
 The sample is a prefix of the workload, compared event by event with the
 GPU outputs of the same workload, so it may never hold more events than the
@@ -23,3 +24,30 @@ def test_oracle_sample_is_the_workload_prefix():
     assert 1 <= n <= n_max
     p = process_momenta("g g > t t~", 1000.0, n, 2)
     np.testing.assert_array_equal(ref, O.me("g g > t t~", p))
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
+    """`bench.py --impl reference` launched like the multi-GPU bench (two
+    ranks under torch.distributed.run): rank 0 times the oracle and prints
+    the one JSON line, the other rank exits 0 without work."""
+    import json
+    import os
+    import socket
+    import subprocess
+    import sys
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl",
+                        "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "MEs/s" and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
